@@ -1,0 +1,322 @@
+"""Benchmark of the majority voter on the 256M-element f32 workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n ELEMS]
+
+One step = one ft_vote of R=3 replicas of n float32 (default n = 2^28, 1 GiB per
+replica): the whole hot path (load, compare, vote, store, statistics, CRC32C per
+4 KiB block).  The metric is voter GB/s with bytes = (R+1) * n * 4 (R reads + 1
+write).  Inputs (4 GiB) exceed the 126 MB L2, so no flush is needed between
+steps.  Prints one JSON line (rank 0).
+
+--impl reference times the CPU oracle (the plain C voter under oracle/) on the
+host cores over a bounded sample of the same workload.
+Under torchrun each rank votes its own copy of the workload on its own GPU
+(weak scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1405_2912_b300 import synth  # noqa: E402
+
+METRIC = "voter input GB/s & % of HBM peak; batched tasks/s; p50/p99 vote latency"
+WORKLOAD = ("3 x 256M float32 replicas (lognormal sigma 2, random sign; +-1..4 ULP on 20% of "
+            "replica 1; bit flips at 1e-6/element in replica 2), abs_tol 1e-6, rel_tol 1e-5, "
+            "CRC32C per 4 KiB block of the voted buffer")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_run(problem, n_sample: int, threads: int) -> tuple:
+    """Time the oracle on the first n_sample elements, split into 4 KiB-aligned
+    chunks voted concurrently on `threads` host threads.  Returns (seconds,
+    bytes)."""
+    import oracle
+    oracle.build()
+    per = max(1024, (n_sample // threads) // 1024 * 1024)
+    bounds = [(s, min(n_sample, s + per)) for s in range(0, n_sample, per)]
+
+    def one(b):
+        s, e = b
+        oracle.vote([r[s:e] for r in problem.replicas], problem.dtype, problem.abs_tol, problem.rel_tol)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, bounds))
+    dt = time.perf_counter() - t0
+    return dt, (problem.R + 1) * n_sample * problem.itemsize
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, problem):
+    cores = host_cores()
+    n_sample = min(problem.n, args.ref_sample)
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        oracle_run(problem, min(n_sample, 1 << 20), cores)
+    times = []
+    nbytes = 0
+    for _ in range(args.steps):
+        dt, nbytes = oracle_run(problem, n_sample, cores)
+        times.append(dt)
+    total = sum(times)
+    gbs = nbytes * args.steps / total / 1e9
+    sample = f"first {n_sample} of {problem.n} elements per step, 4 KiB-aligned chunks on {cores} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "R": problem.R, "n": problem.n},
+            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, problem, ws, rank, local):
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+    R, n = problem.R, problem.n
+    nbytes = n * problem.itemsize
+    reps = [torch.from_numpy(r.view(np.uint8)).to(dev) for r in problem.replicas]
+    out = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    nblk = fv.n_blocks(nbytes)
+    crc = torch.empty(nblk, dtype=torch.int32, device=dev)
+    stats = fv.new_stats(dev)
+    desc = fv.make_desc(reps, out, crc, stats, problem.abs_tol, problem.rel_tol, dtype=problem.dtype, n=n)
+    pd = ctypes.byref(desc)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        fv.check(fv.ft_vote(pd, sh), "ft_vote")
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = fv.ft_launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            starts[k].record(stream)
+            fv.ft_vote(pd, sh)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = fv.ft_launch_count() - launches0
+    clocks = sampler.stop()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]          # ms, per launch pair
+    elapsed = starts[0].elapsed_time(ends[-1]) / 1e3                  # s, whole timed region
+    t_max = max_over_ranks(elapsed, ws)
+    bytes_step = problem.bytes_moved
+    value = bytes_step * args.steps * ws / t_max / 1e9
+    launch_ms = statistics.mean(per)
+    peak, peak_kind = peaks()
+    achieved = bytes_step / (launch_ms / 1e3) / 1e9
+
+    # end to end: host (pinned) replicas -> device, vote, digest + stats -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        host = [torch.from_numpy(r.view(np.uint8)).pin_memory() for r in problem.replicas]
+        crc_h = torch.empty(nblk, dtype=torch.int32).pin_memory()
+        stats_h = torch.empty(18, dtype=torch.int64).pin_memory()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.e2e_steps):
+                for h, d in zip(host, reps):
+                    d.copy_(h, non_blocking=True)
+                fv.ft_vote(pd, sh)
+                crc_h.copy_(crc, non_blocking=True)
+                stats_h.copy_(stats, non_blocking=True)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws)
+        e2e = {"value": round(bytes_step * args.e2e_steps * ws / t_e2e / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": R * nbytes, "d2h_bytes_per_step": 4 * nblk + 144,
+               "steps": args.e2e_steps}
+        del host
+
+    s = fv.parse_stats(stats, R)
+    if rank != 0:
+        return
+    cpu = None
+    if args.cpu_sample > 0 and ws == 1:
+        cores = host_cores()
+        n_s = min(n, args.cpu_sample)
+        dt, b = oracle_run(problem, n_s, cores)
+        cpu = {"value": round(b / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n_s} of {n} elements, 4 KiB-aligned chunks on {cores} threads, one pass"}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "R": R, "n": n, "bytes_per_step": bytes_step,
+                   "l2": "inputs (4 GiB per step) exceed the 126 MB L2; no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "hbm_frac_of_8tbs_spec": round(value / ws / 8000.0, 4),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": args.traffic,
+                     "kernel": "vote_kernel<F32,R=3> + stats reset (one ft_vote)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "result": {"mismatch": s["mismatch"], "no_majority": s["no_majority"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 28, help="elements per replica")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 28, help="elements the oracle votes for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=1 << 26, help="elements per reference step")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        problem = synth.cfg2(n=args.n)
+        run_reference(args, problem)
+        return 0
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    problem = synth.cfg2(n=args.n)
+    run_ours(args, problem, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,222 @@
+/*
+ * ftvote.h -- C ABI of the B300 heterogeneity-aware majority voter.
+ *
+ * The voter is the one of Sec. IV.D of Kicherer & Karl, "Heterogeneity-aware
+ * Fault Tolerance using a Self-Organizing Runtime System": the results of R
+ * redundant executions of a task are compared element by element and the
+ * presumable correct result is selected.  Integer values are compared bit by
+ * bit; floating-point values are equal when they differ by at most a
+ * programmer-set maximum (Sec. IV.D), so that a CPU-vs-GPU rounding difference
+ * is not taken for a fault.  The element type plays the part of the value type
+ * that the paper's dls_register_data() attaches to a buffer (Sec. IV.E).
+ *
+ * Semantics of one vote of n elements of R replicas x_0..x_{R-1}:
+ *   eq(a,b)   integers: equal bit patterns.
+ *             floats (computed in the element's own precision, IEEE
+ *             round-to-nearest, no FMA, no flush-to-zero): equal bit patterns,
+ *             else not equal if either is NaN or +-Inf, else
+ *             |a-b| <= abs_tol  or  |a-b| <= rel_tol * max(|a|,|b|),
+ *             with both tolerances rounded once to the element type.
+ *   support   s_r = #{q : eq(x_r, x_q)}, q = r included.
+ *   winner    w = smallest r with maximal s_r; out[i] = bit copy of x_w[i].
+ *   majority  2 * s_w > R; elements without one are counted in no_majority
+ *             and still receive x_w[i].
+ *   mismatch[r]        #{i : not eq(x_r[i], out[i])}; first_mismatch[r] the
+ *                      smallest such i, -1 if none.  These per-replica counts
+ *                      are the observed fault rates that the paper's
+ *                      fault-aware runtime estimate F_i = R_i / (1 - p_i)
+ *                      consumes (Sec. IV.B).
+ *   block_crc[b]       CRC32C (Castagnoli, reflected 0x82F63B78, init and final
+ *                      XOR 0xFFFFFFFF) of bytes [4096 b, min(4096 (b+1), nbytes))
+ *                      of out, blocks independent; the digest lets a memory
+ *                      manager skip transfers of unchanged data (Sec. IV.A).
+ *
+ * Conventions for every entry point:
+ *   - All data pointers are DEVICE pointers owned by the caller unless stated
+ *     otherwise; descriptors are read from host memory during the call only.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream).  The return code reports
+ *     argument validation and launch errors; results are valid once the
+ *     stream reaches the work.
+ *   - No entry point throws, aborts or falls back to the CPU.
+ */
+#ifndef FTVOTE_H
+#define FTVOTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (all negative except FT_OK) ---- */
+#define FT_OK          0
+#define FT_EINVAL     -1   /* bad argument: dtype, R, NULL, misalignment, aliasing, tolerance */
+#define FT_ENOMEM     -2   /* a library-owned allocation failed                               */
+#define FT_EAGAIN     -3   /* server: over the memory budget / slot limit, or not done yet    */
+#define FT_ETIMEDOUT  -4   /* server: the wait ran out before the request completed           */
+#define FT_ECUDA      -5   /* a CUDA call failed; ft_last_cuda_error() gives the cudaError_t  */
+#define FT_ENOTFOUND  -6   /* server: unknown or already collected ticket                      */
+
+#define FT_MAX_R        8
+#define FT_BLOCK_BYTES  4096u
+
+/* element types; integer types compare bit-wise, tolerances are ignored */
+typedef enum ft_dtype {
+    FT_I32 = 0, FT_U32 = 1, FT_I64 = 2, FT_U64 = 3, FT_U8 = 4, FT_F32 = 5, FT_F64 = 6
+} ft_dtype;
+
+typedef void *ft_stream;   /* cudaStream_t */
+
+/* Per-vote statistics, written by the vote (device memory, 8-byte aligned). */
+typedef struct ft_stats {
+    uint64_t mismatch[FT_MAX_R];        /* entries >= R are written as 0            */
+    int64_t  first_mismatch[FT_MAX_R];  /* -1 = none; entries >= R are written -1   */
+    uint64_t no_majority;
+    int64_t  first_no_majority;         /* -1 = none                                 */
+} ft_stats;
+
+/* One vote.
+ *   replicas[0..R-1]  device pointers, each n * sizeof(dtype) bytes, 16-byte
+ *                     aligned; unused entries are ignored.  Two entries may
+ *                     point to the same buffer.
+ *   out               device, n * sizeof(dtype) bytes, 16-byte aligned; must
+ *                     not overlap any replica.
+ *   block_crc         device, ceil(n * sizeof(dtype) / 4096) uint32 entries,
+ *                     4-byte aligned, or NULL to skip the digest.
+ *   stats             device, one ft_stats, 8-byte aligned (required).
+ *   abs_tol, rel_tol  float dtypes: 0 <= rel_tol <= 1 and 0 <= abs_tol with
+ *                     abs_tol finite once rounded to the element type (a
+ *                     relative tolerance above 100% has no use in a vote);
+ *                     ignored for integer dtypes.                          */
+typedef struct ft_vote_desc {
+    const void *replicas[FT_MAX_R];
+    int32_t     R;          /* 2..8 */
+    int32_t     dtype;      /* ft_dtype */
+    uint64_t    n;          /* elements per replica; 0 is allowed (no work) */
+    double      abs_tol;
+    double      rel_tol;
+    void       *out;
+    uint32_t   *block_crc;
+    ft_stats   *stats;
+} ft_vote_desc;
+
+/* Vote one task (Sec. IV.D).  Two launches on `stream`: a statistics reset and
+ * the persistent voter kernel (128-bit coalesced loads of all R replicas,
+ * vote, store, warp-ballot statistics and the fused per-block CRC32C).
+ * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
+int ft_vote(const ft_vote_desc *desc, ft_stream stream);
+
+/* CRC32C of each block_bytes-sized block of nbytes bytes at buf (device,
+ * 16-byte aligned); out (device) receives ceil(nbytes / block_bytes) values,
+ * the last block being partial.  block_bytes must be a multiple of 4096 in
+ * [4096, 1 << 24].  This is the digest that the memory manager of Sec. IV.A
+ * would compare to skip unchanged transfers.  Returns FT_OK, FT_EINVAL or
+ * FT_ECUDA. */
+int ft_digest(const void *buf, uint64_t nbytes, uint32_t block_bytes,
+              uint32_t *out, ft_stream stream);
+
+/* ---- batched form: many tasks in one persistent, graph-captured launch ---- */
+
+/* Tuning of the batched kernel.  tile_blocks = 4 KiB blocks per work tile
+ * (1..64); ctas_per_sm = resident CTAs per SM requested (1..8); 0 = choose by
+ * autotuning when the plan is created. */
+typedef struct ft_tune {
+    int32_t tile_blocks;
+    int32_t ctas_per_sm;
+} ft_tune;
+
+typedef struct ft_plan ft_plan;   /* library-owned */
+
+/* Build a plan for ntasks votes (each described as for ft_vote; every task
+ * has its own dtype, R, tolerances and outputs; element indices in the
+ * statistics are local to the task).  The plan copies the descriptors to a
+ * device task table, autotunes the tile size and CTA count when `tune` is NULL
+ * or holds zeros (timing real launches on the plan's buffers, which it
+ * overwrites), and captures a CUDA graph of the reset + batched kernel.
+ * The caller keeps every buffer alive and in place until ft_plan_destroy.
+ * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
+int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks,
+                   const ft_tune *tune);
+
+/* Replay the plan's graph on `stream`: every task of the plan is voted. */
+int ft_vote_batched(ft_plan *plan, ft_stream stream);
+
+/* Launch the batched kernel without the graph (same work, two launches). */
+int ft_vote_batched_nograph(ft_plan *plan, ft_stream stream);
+
+/* Vote n tasks with one ft_vote each (two launches per task, in order, on
+ * `stream`): the unbatched form that the batched plan is measured against. */
+int ft_vote_many(const ft_vote_desc *descs, int32_t n, ft_stream stream);
+
+/* The tuning the plan uses. */
+int ft_plan_tune(const ft_plan *plan, ft_tune *out);
+
+int ft_plan_destroy(ft_plan *plan);
+
+/* ---- serving form: continuous batching of vote requests ---- */
+
+typedef struct ft_server ft_server;   /* library-owned */
+
+typedef struct ft_server_config {
+    uint64_t mem_budget_bytes;  /* admission budget: sum over admitted, not yet
+                                   collected requests of (R+1) * n * sizeof(dtype) */
+    int32_t  max_slots;         /* most requests packed into one batch (1..65536) */
+    int32_t  streams;           /* batches in flight at once (1..8)               */
+    int32_t  tile_blocks;       /* batched-kernel tile (0 = 8)                     */
+    int32_t  max_inflight;      /* most admitted, not yet collected requests (0 = 65536) */
+} ft_server_config;
+
+typedef struct ft_result {
+    int32_t  status;            /* FT_OK or the FT_ECUDA of the batch            */
+    int32_t  R;
+    uint64_t n;
+    ft_stats stats;             /* copy of the request's statistics              */
+    double   submit_us;         /* host clock (monotonic, microseconds) at submit */
+    double   done_us;           /* host clock when the batch's completion callback ran */
+} ft_result;
+
+/* Start a server: one host thread that packs admitted requests into batches
+ * and launches them on `streams` CUDA streams of the current device.
+ * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
+int ft_server_create(ft_server **srv, const ft_server_config *cfg);
+
+/* Admit one request (the replicas must already hold the duplicated results).
+ * The server keeps the descriptor; the caller keeps every buffer alive and
+ * unchanged until ft_poll has returned FT_OK for the ticket.  desc->stats may
+ * be NULL: the server then keeps the statistics itself and returns them in
+ * the ft_result only.  Returns FT_OK with *ticket set, FT_EAGAIN when the
+ * request does not fit the free budget or the in-flight limit right now
+ * (nothing is kept; retry later), or FT_EINVAL. */
+int ft_submit(ft_server *srv, const ft_vote_desc *desc, uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (0 = do not wait, < 0 = wait without a
+ * limit) for a request.  FT_OK: done, *res filled, ticket retired and its
+ * budget released.  FT_ETIMEDOUT: not done within the limit (the request
+ * stays in flight; poll again).  FT_ENOTFOUND: unknown ticket. */
+int ft_poll(ft_server *srv, uint64_t ticket, int64_t timeout_us, ft_result *res);
+
+/* Hold back (paused != 0) or release the launching of admitted requests.
+ * While paused, requests are admitted and queued on the host but no batch
+ * starts, so ft_poll on them times out: the host-side way to exercise the
+ * bounded wait without stalling anything on the GPU.  Returns FT_OK. */
+int ft_server_pause(ft_server *srv, int32_t paused);
+
+/* Stop the server after the batches in flight complete; requests not yet
+ * launched and uncollected tickets are dropped.  No other thread may use the
+ * server during or after this call.  Returns FT_OK. */
+int ft_server_destroy(ft_server *srv);
+
+/* The monotonic host clock (microseconds) of ft_result.submit_us / done_us. */
+double ft_clock_us(void);
+
+/* ---- misc ---- */
+const char *ft_strerror(int code);
+int         ft_last_cuda_error(void);     /* cudaError_t of the last FT_ECUDA in this thread */
+uint64_t    ft_launch_count(void);        /* kernels this library has launched (all threads) */
+const char *ft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTVOTE_H */

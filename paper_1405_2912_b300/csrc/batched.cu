@@ -1,0 +1,505 @@
+// batched.cu -- the batched voter: thousands of tasks of uneven size and mixed
+// element type voted by persistent kernels that pull work tiles from a device
+// counter, captured together with the statistics reset in one CUDA graph
+// (ft_plan_create / ft_vote_batched), and the tile-size / CTA autotuner.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "batched.h"
+#include "common.cuh"
+#include "runtime.h"
+
+namespace ftv {
+
+// ---------------------------------------------------------------------------
+// K3: persistent batched voter for one (kind, R) group.  A warp claims the
+// next tile with one atomic, looks up its task in the tile map, votes the
+// tile's 4 KiB blocks (and the task's partial last block when the tile holds
+// it), and flushes its per-task statistics whenever it moves to another task.
+// Tiles are claimed in increasing order, so a warp meets each task's blocks in
+// increasing order and the first index it sees per replica is its minimum.
+// ---------------------------------------------------------------------------
+template <int K, int R, int W>
+__global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *s_comb = s_crc + kCrcWords;
+    uint4 *tiles = reinterpret_cast<uint4 *>(s_comb + kCombWords);
+    load_crc_tables(s_crc, s_comb);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint4 *tile = tiles + w * kTileVecs;
+    CrcLane L;
+    L.init(lane);
+    LaneStats<R> st;
+    st.init();
+    int cur = -1;
+    ft_stats *cur_stats = nullptr;
+    for (;;) {
+        unsigned long long tg = 0;
+        if (lane == 0) tg = atomicAdd(g.counter, 1ull);
+        tg = __shfl_sync(0xFFFFFFFFu, tg, 0);
+        if (tg >= g.total_tiles) break;
+        const int t = (int)g.tile_task[tg];
+        const TaskArgs a = g.tasks[t];
+        if (t != cur) {
+            if (cur >= 0) st.flush(cur_stats, lane);
+            st.init();
+            cur = t;
+            cur_stats = a.stats;
+        }
+        const unsigned long long k = tg - g.tile_first[t];
+        const unsigned long long b0 = k * (unsigned long long)g.tile_blocks;
+        const unsigned long long b1 = min(b0 + (unsigned long long)g.tile_blocks, a.nfull);
+        for (unsigned long long b = b0; b < b1; ++b)
+            vote_full_block<K, R>(a, b, b + 1 < b1 ? b + 1 : ~0ull, tile, s_crc, s_comb, L, st, lane);
+        if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
+            LaneStats<R> ts;
+            ts.init();
+            vote_tail_block<K, R>(a, a.nfull, tile, s_crc, ts, lane);
+            st.merge(ts);
+        }
+    }
+    if (cur >= 0) st.flush(cur_stats, lane);
+}
+
+constexpr int kBatchWarps = 16;
+
+template <int K, int R>
+static const void *group_fn()
+{
+    return reinterpret_cast<const void *>(batched_kernel<K, R, kBatchWarps>);
+}
+
+template <int K>
+static const void *group_fn_k(int R)
+{
+    switch (R) {
+    case 2: return group_fn<K, 2>();
+    case 3: return group_fn<K, 3>();
+    case 4: return group_fn<K, 4>();
+    case 5: return group_fn<K, 5>();
+    case 6: return group_fn<K, 6>();
+    case 7: return group_fn<K, 7>();
+    case 8: return group_fn<K, 8>();
+    default: return nullptr;
+    }
+}
+
+static const void *group_kernel(int kind, int R)
+{
+    switch (kind) {
+    case K_F32: return group_fn_k<K_F32>(R);
+    case K_F64: return group_fn_k<K_F64>(R);
+    case K_B1: return group_fn_k<K_B1>(R);
+    case K_B4: return group_fn_k<K_B4>(R);
+    case K_B8: return group_fn_k<K_B8>(R);
+    default: return nullptr;
+    }
+}
+
+int group_occupancy(int kind, int R, int *sms, int *per_sm)
+{
+    const void *fn = group_kernel(kind, R);
+    if (!fn) return FT_EINVAL;
+    return occupancy(fn, kBatchWarps * 32, Smem::bytes(kBatchWarps), sms, per_sm);
+}
+
+int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
+{
+    const void *fn = group_kernel(g.kind, g.R);
+    if (!fn) return FT_EINVAL;
+    if (g.total_tiles == 0) return FT_OK;
+    const size_t smem = Smem::bytes(kBatchWarps);
+    int sms = 0, per_sm = 0;
+    int rc = occupancy(fn, kBatchWarps * 32, smem, &sms, &per_sm);
+    if (rc != FT_OK) return rc;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    unsigned long long grid = (unsigned long long)sms * per_sm;
+    const unsigned long long need = (g.total_tiles + kBatchWarps - 1) / kBatchWarps;
+    if (grid > need) grid = need;
+    GroupDev arg = g;
+    void *params[] = {&arg};
+    const cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kBatchWarps * 32), params, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return check_launch(1);
+}
+
+__global__ void batch_reset_kernel(const TaskArgs *tasks, int ntasks, unsigned long long *counters, int ncounters)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = i / (FT_MAX_R + 1), f = i % (FT_MAX_R + 1);
+    if (t < ntasks) reset_stats(tasks[t].stats, f);
+    if (i < ncounters) counters[i] = 0;
+}
+
+int launch_batch_reset(const TaskArgs *tasks, int ntasks, unsigned long long *counters, int ncounters,
+                       cudaStream_t s)
+{
+    const int items = std::max(ntasks * (FT_MAX_R + 1), ncounters);
+    if (items == 0) return FT_OK;
+    batch_reset_kernel<<<(items + 255) / 256, 256, 0, s>>>(tasks, ntasks, counters, ncounters);
+    return check_launch(1);
+}
+
+__global__ void stats_scatter_kernel(const ft_stats *src, ft_stats *const *dst, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = i / 18, f = i % 18;
+    if (t < n && dst[t]) reinterpret_cast<long long *>(dst[t])[f] = reinterpret_cast<const long long *>(src + t)[f];
+}
+
+int launch_stats_scatter(const ft_stats *src, ft_stats *const *dst, int n, cudaStream_t s)
+{
+    if (n == 0) return FT_OK;
+    stats_scatter_kernel<<<(n * 18 + 255) / 256, 256, 0, s>>>(src, dst, n);
+    return check_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side batch layout, shared by plans and the server.
+// ---------------------------------------------------------------------------
+void BatchLayout::build(const std::vector<TaskArgs> &in, int tile_blocks)
+{
+    tile_blocks_ = tile_blocks;
+    tasks.clear();
+    groups.clear();
+    tile_first.clear();
+    tile_task.clear();
+    // order tasks by (kind, R), stable, so that each group is contiguous
+    std::vector<int> order(in.size());
+    for (size_t i = 0; i < in.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return std::make_pair(in[x].kind, in[x].R) < std::make_pair(in[y].kind, in[y].R);
+    });
+    user_index.assign(order.begin(), order.end());
+    for (int idx : order) tasks.push_back(in[idx]);
+    tile_first.resize(tasks.size());
+    for (size_t t = 0; t < tasks.size();) {
+        GroupHost gh;
+        gh.kind = tasks[t].kind;
+        gh.R = tasks[t].R;
+        gh.t0 = (int)t;
+        gh.tile0 = tile_task.size();
+        unsigned long long g_tiles = 0;
+        while (t < tasks.size() && tasks[t].kind == gh.kind && tasks[t].R == gh.R) {
+            const TaskArgs &a = tasks[t];
+            const unsigned long long nblk = a.nfull + (a.tail_bytes ? 1 : 0);
+            const unsigned long long nt = (nblk + tile_blocks - 1) / tile_blocks;
+            tile_first[t] = g_tiles;
+            for (unsigned long long k = 0; k < nt; ++k) tile_task.push_back((uint32_t)t);
+            g_tiles += nt;
+            ++t;
+        }
+        gh.t1 = (int)t;
+        gh.tiles = g_tiles;
+        groups.push_back(gh);
+    }
+}
+
+size_t BatchLayout::device_bytes() const
+{
+    return align(sizeof(TaskArgs) * tasks.size()) + align(8 * tile_first.size()) + align(4 * tile_task.size()) +
+           align(8 * groups.size());
+}
+
+// Packs the layout into `host` (device_bytes() long) as it must appear at
+// device address `dev`, and fills the GroupDev descriptors.
+void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
+{
+    size_t off = 0;
+    const size_t o_tasks = off;
+    off += align(sizeof(TaskArgs) * tasks.size());
+    const size_t o_first = off;
+    off += align(8 * tile_first.size());
+    const size_t o_map = off;
+    off += align(4 * tile_task.size());
+    const size_t o_cnt = off;
+    if (!tasks.empty()) std::memcpy(host + o_tasks, tasks.data(), sizeof(TaskArgs) * tasks.size());
+    if (!tile_first.empty()) std::memcpy(host + o_first, tile_first.data(), 8 * tile_first.size());
+    if (!tile_task.empty()) std::memcpy(host + o_map, tile_task.data(), 4 * tile_task.size());
+    std::memset(host + o_cnt, 0, 8 * groups.size());
+    gd.clear();
+    for (size_t i = 0; i < groups.size(); ++i) {
+        const GroupHost &gh = groups[i];
+        GroupDev g;
+        std::memset(&g, 0, sizeof(g));
+        g.tasks = reinterpret_cast<const TaskArgs *>(dev + o_tasks);
+        g.tile_task = reinterpret_cast<const uint32_t *>(dev + o_map) + gh.tile0;
+        g.tile_first = reinterpret_cast<const unsigned long long *>(dev + o_first);
+        g.total_tiles = gh.tiles;
+        g.counter = reinterpret_cast<unsigned long long *>(dev + o_cnt) + i;
+        g.tile_blocks = tile_blocks_;
+        g.kind = gh.kind;
+        g.R = gh.R;
+        gd.push_back(g);
+    }
+    counters_dev = reinterpret_cast<unsigned long long *>(dev + o_cnt);
+    tasks_dev = reinterpret_cast<const TaskArgs *>(dev + o_tasks);
+}
+
+int launch_batch(const BatchLayout &L, const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s)
+{
+    int rc = launch_batch_reset(L.tasks_dev, (int)L.tasks.size(), L.counters_dev, (int)gd.size(), s);
+    if (rc != FT_OK) return rc;
+    for (const GroupDev &g : gd)
+        if ((rc = launch_group(g, ctas_per_sm, s)) != FT_OK) return rc;
+    return FT_OK;
+}
+
+}  // namespace ftv
+
+// ---------------------------------------------------------------------------
+// Plans
+// ---------------------------------------------------------------------------
+struct ft_plan {
+    ftv::BatchLayout layout;
+    std::vector<ftv::TaskArgs> args;
+    std::vector<ftv::GroupDev> gd;
+    uint8_t *dev = nullptr;
+    size_t dev_bytes = 0;
+    ft_tune tune{0, 0};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+    unsigned long long graph_kernels = 0;   // kernel launches one replay makes
+};
+
+namespace ftv {
+
+static int upload_layout(ft_plan *p, int tile_blocks)
+{
+    p->layout.build(p->args, tile_blocks);
+    const size_t need = p->layout.device_bytes();
+    if (need > p->dev_bytes) {
+        if (p->dev) cudaFree(p->dev);
+        p->dev = nullptr;
+        p->dev_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->dev, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? FT_ENOMEM : cuda_fail(e);
+        }
+        p->dev_bytes = need;
+    }
+    std::vector<uint8_t> host(need);
+    p->layout.pack(host.data(), p->dev, p->gd);
+    cudaError_t e = cudaMemcpy(p->dev, host.data(), need, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? FT_OK : cuda_fail(e);
+}
+
+// In-process autotune cache keyed by a coarse signature of the batch.
+static std::mutex g_tune_mu;
+static std::map<std::string, ft_tune> g_tune_cache;
+
+static std::string signature(const std::vector<TaskArgs> &args)
+{
+    unsigned long long bytes = 0, blocks = 0;
+    std::map<std::pair<int, int>, int> mix;
+    for (const TaskArgs &a : args) {
+        blocks += a.nfull + (a.tail_bytes ? 1 : 0);
+        bytes += (a.nfull * 4096ull + a.tail_bytes) * (a.R + 1);
+        mix[{a.kind, a.R}]++;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    char buf[256];
+    int lb = 0;
+    while ((bytes >> lb) > 1) ++lb;
+    std::snprintf(buf, sizeof buf, "dev%d:n%zu:b2^%d:blk%llu", dev, args.size(), lb, blocks / std::max<size_t>(1, args.size()));
+    std::string s(buf);
+    for (auto &kv : mix) s += ":" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second);
+    return s;
+}
+
+static int time_config(ft_plan *p, const ft_tune &t, cudaStream_t s, float *best_ms)
+{
+    int rc = upload_layout(p, t.tile_blocks);
+    if (rc != FT_OK) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    rc = launch_batch(p->layout, p->gd, t.ctas_per_sm, s);   // warm-up
+    for (int rep = 0; rep < 3 && rc == FT_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = launch_batch(p->layout, p->gd, t.ctas_per_sm, s);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best_ms = best;
+    return rc;
+}
+
+static int autotune(ft_plan *p, ft_tune *out)
+{
+    const std::string key = signature(p->args);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            return FT_OK;
+        }
+    }
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int max_occ = 1;
+    for (const TaskArgs &a : p->args) {
+        int sms = 0, occ = 0;
+        if (group_occupancy(a.kind, a.R, &sms, &occ) == FT_OK) max_occ = std::max(max_occ, occ);
+    }
+    const int tiles[] = {1, 2, 4, 8, 16, 32};
+    ft_tune best{8, 0};
+    float best_ms = 1e30f;
+    int rc = FT_OK;
+    for (int tb : tiles) {
+        for (int cps = 1; cps <= max_occ && rc == FT_OK; ++cps) {
+            ft_tune t{tb, cps};
+            float ms = 0;
+            rc = time_config(p, t, s, &ms);
+            if (rc == FT_OK && ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc != FT_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    *out = best;
+    return FT_OK;
+}
+
+static int capture(ft_plan *p)
+{
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = FT_OK;
+    const unsigned long long before = g_launches.load();
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) rc = cuda_fail(e);
+    if (rc == FT_OK) {
+        rc = launch_batch(p->layout, p->gd, p->tune.ctas_per_sm, s);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (rc == FT_OK && e != cudaSuccess) rc = cuda_fail(e);
+        if (rc == FT_OK) {
+            p->graph = g;
+            if ((e = cudaGraphInstantiate(&p->exec, g, 0)) != cudaSuccess) rc = cuda_fail(e);
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    cudaStreamDestroy(s);
+    // the launches recorded during capture did not run; a replay makes them
+    p->graph_kernels = g_launches.load() - before;
+    g_launches.fetch_sub(p->graph_kernels, std::memory_order_relaxed);
+    return rc;
+}
+
+}  // namespace ftv
+
+extern "C" {
+
+int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks, const ft_tune *tune)
+{
+    using namespace ftv;
+    if (!plan || ntasks < 0 || (ntasks > 0 && !tasks)) return FT_EINVAL;
+    *plan = nullptr;
+    if (tune && ((tune->tile_blocks && (tune->tile_blocks < 1 || tune->tile_blocks > 64)) ||
+                 tune->ctas_per_sm < 0 || tune->ctas_per_sm > 8))
+        return FT_EINVAL;
+    ft_plan *p = new (std::nothrow) ft_plan();
+    if (!p) return FT_ENOMEM;
+    cudaGetDevice(&p->device);
+    for (int i = 0; i < ntasks; ++i) {
+        int rc = validate_desc(&tasks[i]);
+        if (rc != FT_OK) {
+            delete p;
+            return rc;
+        }
+        p->args.push_back(make_task_args(&tasks[i]));
+    }
+    int rc = FT_OK;
+    if (!tune || tune->tile_blocks == 0 || tune->ctas_per_sm == 0) {
+        ft_tune t{};
+        rc = autotune(p, &t);
+        if (rc == FT_OK && tune && tune->tile_blocks) t.tile_blocks = tune->tile_blocks;
+        if (rc == FT_OK && tune && tune->ctas_per_sm) t.ctas_per_sm = tune->ctas_per_sm;
+        p->tune = t;
+    } else {
+        p->tune = *tune;
+    }
+    if (rc == FT_OK) rc = upload_layout(p, p->tune.tile_blocks);
+    if (rc == FT_OK) rc = capture(p);
+    if (rc != FT_OK) {
+        ft_plan_destroy(p);
+        return rc;
+    }
+    *plan = p;
+    return FT_OK;
+}
+
+int ft_vote_batched(ft_plan *p, ft_stream stream)
+{
+    if (!p || !p->exec) return FT_EINVAL;
+    const cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ftv::cuda_fail(e);
+    ftv::g_launches.fetch_add(p->graph_kernels, std::memory_order_relaxed);
+    return FT_OK;
+}
+
+int ft_vote_batched_nograph(ft_plan *p, ft_stream stream)
+{
+    if (!p) return FT_EINVAL;
+    return ftv::launch_batch(p->layout, p->gd, p->tune.ctas_per_sm, static_cast<cudaStream_t>(stream));
+}
+
+int ft_plan_tune(const ft_plan *p, ft_tune *out)
+{
+    if (!p || !out) return FT_EINVAL;
+    *out = p->tune;
+    return FT_OK;
+}
+
+int ft_plan_destroy(ft_plan *p)
+{
+    if (!p) return FT_EINVAL;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->dev) cudaFree(p->dev);
+    delete p;
+    return FT_OK;
+}
+
+int ft_vote_many(const ft_vote_desc *descs, int32_t n, ft_stream stream)
+{
+    if (n < 0 || (n > 0 && !descs)) return FT_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const int rc = ftv::vote_desc(&descs[i], static_cast<cudaStream_t>(stream), nullptr);
+        if (rc != FT_OK) return rc;
+    }
+    return FT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// batched.h -- host-side layout of a batch of vote tasks in device memory:
+// the task table ordered by (kind, R) group, each task's first tile, and the
+// tile -> task map that the persistent batched kernel reads.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+#include "runtime.h"
+
+namespace ftv {
+
+struct GroupHost {
+    int kind, R;
+    int t0, t1;                 // task range in the ordered table
+    size_t tile0;               // offset of the group's tiles in tile_task
+    unsigned long long tiles;
+};
+
+struct BatchLayout {
+    std::vector<TaskArgs> tasks;                  // ordered by (kind, R)
+    std::vector<int> user_index;                  // tasks[i] is the caller's task user_index[i]
+    std::vector<GroupHost> groups;
+    std::vector<unsigned long long> tile_first;   // per ordered task: first tile in its group
+    std::vector<uint32_t> tile_task;              // per tile (all groups back to back)
+    int tile_blocks_ = 8;
+    // set by pack(): device addresses of the table and the counters
+    const TaskArgs *tasks_dev = nullptr;
+    unsigned long long *counters_dev = nullptr;
+
+    static size_t align(size_t x) { return (x + 255) & ~size_t(255); }
+    void build(const std::vector<TaskArgs> &in, int tile_blocks);
+    size_t device_bytes() const;
+    void pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd);
+};
+
+int launch_batch(const BatchLayout &L, const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s);
+
+}  // namespace ftv

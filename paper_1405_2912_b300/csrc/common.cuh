@@ -1,0 +1,628 @@
+// common.cuh -- device building blocks of the voter: typed comparison, the
+// R-way vote, per-replica statistics and the fused CRC32C of a 4 KiB block.
+//
+// Work decomposition (shared by the single-task and the batched kernels): one
+// warp owns one 4096-byte block of the voted output at a time.  Lane l loads
+// the 16-byte vectors l, l+32, ..., l+224 of the block from every replica
+// (coalesced 128-bit loads), votes their elements in registers, stores the
+// voted vectors (coalesced 128-bit stores) and also writes them into a padded
+// per-warp shared-memory tile.  It then reads back the 128 contiguous bytes
+// [128 l, 128 l + 128) of the block from the tile and runs CRC32C over them;
+// the 32 lane CRCs are shifted to their place in the block by a per-lane
+// GF(2) multiplication and XOR-reduced across the warp.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ftvote.h"
+
+namespace ftv {
+
+// ---------------------------------------------------------------------------
+// CRC32C arithmetic over GF(2), reflected representation.
+// A 32-bit register value c stands for the polynomial whose x^(31-j)
+// coefficient is bit j of c.  Processing a message M from register 0 yields
+// M(x) * x^32 mod P(x); a zero byte multiplies the register by x^8.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPoly = 0x82F63B78u;          // reflected Castagnoli polynomial
+
+__host__ __device__ constexpr uint32_t gf_mulx(uint32_t a)
+{
+    return (a >> 1) ^ ((a & 1u) ? kPoly : 0u);
+}
+
+// a(x) * b(x) mod P(x)
+__host__ __device__ constexpr uint32_t gf_mul(uint32_t a, uint32_t b)
+{
+    uint32_t r = 0;
+    for (int j = 0; j < 32; ++j) {
+        if (b & (0x80000000u >> j)) r ^= a;
+        a = gf_mulx(a);
+    }
+    return r;
+}
+
+// x^(8 * nbytes) mod P(x): the operator "append nbytes zero bytes".
+__host__ __device__ constexpr uint32_t gf_xpow8(uint64_t nbytes)
+{
+    uint32_t result = 0x80000000u;   // x^0
+    uint32_t base = 0x40000000u;     // x^1
+    uint64_t e = nbytes * 8u;
+    while (e) {
+        if (e & 1u) result = gf_mul(result, base);
+        base = gf_mul(base, base);
+        e >>= 1;
+    }
+    return result;
+}
+
+struct CrcTables {
+    uint32_t slice[4][256];     // slicing-by-4 byte tables
+    uint32_t comb[8][16][32];   // comb[p][v][l] = (v << 4p) * x^(8*128*(31-l))
+    uint32_t shift4096[8][16];  // shift4096[p][v] = (v << 4p) * x^(8*4096)
+    uint32_t init4096;          // 0xFFFFFFFF * x^(8*4096): initial-value term of a full block
+};
+
+constexpr CrcTables make_crc_tables()
+{
+    CrcTables t{};
+    for (uint32_t b = 0; b < 256; ++b) {
+        uint32_t c = b;
+        for (int k = 0; k < 8; ++k) c = gf_mulx(c);
+        t.slice[0][b] = c;
+    }
+    for (int k = 1; k < 4; ++k)
+        for (uint32_t b = 0; b < 256; ++b) {
+            uint32_t prev = t.slice[k - 1][b];
+            t.slice[k][b] = (prev >> 8) ^ t.slice[0][prev & 0xFFu];
+        }
+    for (int l = 0; l < 32; ++l) {
+        uint32_t K = gf_xpow8(128ull * (31 - l));
+        for (int p = 0; p < 8; ++p) {
+            uint32_t bit[4] = {};
+            for (int q = 0; q < 4; ++q) bit[q] = gf_mul(1u << (4 * p + q), K);
+            for (uint32_t v = 0; v < 16; ++v) {
+                uint32_t acc = 0;
+                for (int q = 0; q < 4; ++q)
+                    if (v & (1u << q)) acc ^= bit[q];
+                t.comb[p][v][l] = acc;
+            }
+        }
+    }
+    {
+        uint32_t K = gf_xpow8(4096);
+        for (int p = 0; p < 8; ++p)
+            for (uint32_t v = 0; v < 16; ++v) t.shift4096[p][v] = gf_mul(v << (4 * p), K);
+        t.init4096 = gf_mul(0xFFFFFFFFu, K);
+    }
+    return t;
+}
+
+constexpr CrcTables kCrcHost = make_crc_tables();
+// Device copy, initialised at load time from the compile-time tables.
+__device__ const CrcTables g_crc = kCrcHost;
+
+constexpr int kBlockBytes = 4096;
+constexpr int kTileVecs = 288;      // 256 vectors + one 16-byte pad per 128 bytes
+constexpr int kCombWords = 8 * 16 * 32;
+constexpr int kCrcRowWords = 64;    // one 256-byte row per byte value: 4 tables x 16 copies
+constexpr int kCrcWords = 256 * kCrcRowWords;
+constexpr uint64_t kNone = ~0ull;   // "no index yet"; reads as -1 through int64
+
+// Shared-memory layout of a CTA: the slicing tables (row e holds T_k[e] for
+// k = 0..3, 16 copies each), the per-lane combine tables, then one padded
+// tile per warp.
+struct Smem {
+    static __host__ __device__ constexpr size_t bytes(int warps)
+    {
+        return sizeof(uint32_t) * (kCrcWords + kCombWords) + size_t(warps) * kTileVecs * 16;
+    }
+};
+
+__device__ __forceinline__ void load_crc_tables(uint32_t *s_crc, uint32_t *s_comb)
+{
+    for (int i = threadIdx.x; i < kCrcWords; i += blockDim.x) {
+        const int e = i >> 6, k = (i >> 4) & 3;
+        s_crc[i] = g_crc.slice[k][e];
+    }
+    const uint4 *csrc = reinterpret_cast<const uint4 *>(&g_crc.comb[0][0][0]);
+    uint4 *cdst = reinterpret_cast<uint4 *>(s_comb);
+    for (int i = threadIdx.x; i < kCombWords / 4; i += blockDim.x) cdst[i] = csrc[i];
+}
+
+// Per-lane constants of the table lookups.  Lane l reads copy l % 16.  In
+// lookup i of a slicing step, lanes 0-15 read table T_{3-i} at byte i of the
+// register and lanes 16-31 read T_{3-(i^1)} at byte i^1: tables of even index
+// sit in banks 0-15 and odd ones in banks 16-31, so the two half-warps never
+// share a bank and each lookup is one wavefront.  Each address is built by one
+// byte permute: byte 0 = the lane's offset within the row, byte 1 = the data
+// byte (the row), bytes 2-3 = 0.
+struct CrcLane {
+    uint32_t off01, off23;   // offsets for lookups 0,1 (bytes 0,1) and 2,3
+    uint32_t sel[4];         // byte-permute selectors
+    __device__ __forceinline__ void init(int lane)
+    {
+        const int h = lane >> 4, c = lane & 15;
+        uint32_t o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = h ? (i ^ 1) : i;
+            o[i] = (uint32_t)(((3 - m) * 16 + c) * 4);
+            sel[i] = 0x6600u | ((uint32_t)m << 4) | (4u + (i & 1));
+        }
+        off01 = o[0] | (o[1] << 8);
+        off23 = o[2] | (o[3] << 8);
+    }
+};
+
+__device__ __forceinline__ uint32_t lds_at(const uint32_t *base, uint32_t byte_off)
+{
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(base) + byte_off);
+}
+
+// One slicing-by-4 step: the register after four more message bytes, given
+// c = register XOR (next four bytes, little-endian).
+__device__ __forceinline__ uint32_t crc_step4(const uint32_t *s_crc, const CrcLane &L, uint32_t c)
+{
+    const uint32_t a = lds_at(s_crc, __byte_perm(c, L.off01, L.sel[0]));
+    const uint32_t b = lds_at(s_crc, __byte_perm(c, L.off01, L.sel[1]));
+    const uint32_t d = lds_at(s_crc, __byte_perm(c, L.off23, L.sel[2]));
+    const uint32_t e = lds_at(s_crc, __byte_perm(c, L.off23, L.sel[3]));
+    return a ^ b ^ d ^ e;
+}
+
+// One byte step with table T_0 (slow paths only).
+__device__ __forceinline__ uint32_t crc_step1(const uint32_t *s_crc, uint32_t c, uint32_t byte)
+{
+    return s_crc[((c ^ byte) & 0xFFu) * kCrcRowWords] ^ (c >> 8);
+}
+
+__device__ __forceinline__ uint32_t warp_xor(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Lane l's CRC of bytes [128 l, 128 l + 128) of the tile, shifted to its place
+// in the 4096-byte block and XOR-combined over the warp: the raw (zero-init)
+// register of the whole block.
+__device__ __forceinline__ uint32_t tile_crc_full(const uint4 *tile, const uint32_t *s_crc,
+                                                  const uint32_t *s_comb, const CrcLane &L, int lane)
+{
+    uint32_t c = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const uint4 q = tile[9 * lane + t];
+        c = crc_step4(s_crc, L, c ^ q.x);
+        c = crc_step4(s_crc, L, c ^ q.y);
+        c = crc_step4(s_crc, L, c ^ q.z);
+        c = crc_step4(s_crc, L, c ^ q.w);
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) r ^= s_comb[(p * 16 + ((c >> (4 * p)) & 15u)) * 32 + lane];
+    return warp_xor(r);
+}
+
+// Raw register of the first `len` (< 4096, any) bytes of the tile; slow path
+// for a partial last block.
+static __device__ __noinline__ uint32_t tile_crc_partial(const uint4 *tile, const uint32_t *s_crc, uint32_t len, int lane)
+{
+    const uint32_t start = 128u * lane;
+    const uint32_t seg = len > start ? min(128u, len - start) : 0u;
+    const uint8_t *bytes = reinterpret_cast<const uint8_t *>(tile) + 144u * lane;
+    uint32_t c = 0;
+    for (uint32_t k = 0; k < seg; ++k) c = crc_step1(s_crc, c, bytes[k]);
+    const uint32_t after = len > start + 128u ? len - start - 128u : 0u;
+    c = gf_mul(c, gf_xpow8(after));
+    return warp_xor(c);
+}
+
+// Multiply by x^(8*4096) with the shared nibble tables (uniform across the warp).
+__device__ __forceinline__ uint32_t shift_4096(uint32_t c)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) r ^= g_crc.shift4096[p][(c >> (4 * p)) & 15u];
+    return r;
+}
+
+__device__ __forceinline__ int tile_index(int v) { return v + (v >> 3); }
+
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Element kinds.  Integer types compare bits, so only their width matters.
+// Each kind has a per-call context (its tolerances), a per-replica prepared
+// value P and the exact comparison eq(P, P).
+// ---------------------------------------------------------------------------
+enum Kind { K_F32 = 0, K_F64 = 1, K_B1 = 2, K_B4 = 3, K_B8 = 4 };
+
+template <int K> struct Elem;
+
+// f32.  With rel_tol <= 1 and a finite abs_tol (both checked by the host),
+//   eq(a,b) = bits(a) == bits(b)  or  |a-b| <= max(u_a, u_b),
+//   u_x = min(max(abs_tol, rel_tol*|x|), FLT_MAX)
+// equals the rule "equal bits; else NaN/Inf -> unequal; else |a-b| <= abs_tol
+// or |a-b| <= rel_tol*max(|a|,|b|)": rounding is monotone, so
+// max(rel*|a|, rel*|b|) = rel*max(|a|,|b|); a NaN or infinite operand makes
+// |a-b| NaN or +Inf, which the clamp of u to FLT_MAX rejects; and for finite
+// operands the clamp is inactive.
+template <> struct Elem<K_F32> {
+    using V = uint32_t;
+    static constexpr int kSize = 4;
+    static constexpr bool kBitsFirst = false;
+    struct Ctx { float a, r; };
+    struct P { uint32_t bits; float v, u; };
+    static __device__ __forceinline__ Ctx ctx(double a, double r) { return {__double2float_rn(a), __double2float_rn(r)}; }
+    static __device__ __forceinline__ P prep(V x, Ctx c)
+    {
+        const float v = __uint_as_float(x);
+        return {x, v, fminf(fmaxf(c.a, __fmul_rn(c.r, fabsf(v))), 3.402823466e38f)};
+    }
+    static __device__ __forceinline__ bool eq(const P &x, const P &y, Ctx)
+    {
+        return (x.bits == y.bits) | (fabsf(__fsub_rn(x.v, y.v)) <= fmaxf(x.u, y.u));
+    }
+    static __device__ __forceinline__ V get(const uint4 &v, int e) { return (&v.x)[e]; }
+    static __device__ __forceinline__ void set(uint4 &v, int e, V x) { (&v.x)[e] = x; }
+};
+
+// f64.  FP64 arithmetic is slow on this part, so the rule is evaluated in FP64
+// only for operands whose bits differ.
+template <> struct Elem<K_F64> {
+    using V = unsigned long long;
+    static constexpr int kSize = 8;
+    static constexpr bool kBitsFirst = true;
+    struct Ctx { double a, r; };
+    struct P { V bits; };
+    static __device__ __forceinline__ Ctx ctx(double a, double r) { return {a, r}; }
+    static __device__ __forceinline__ P prep(V x, Ctx) { return {x}; }
+    static __device__ __noinline__ bool eq_slow(V ia, V ib, double ta, double tr)
+    {
+        const bool fin = ((ia & 0x7FFFFFFFFFFFFFFFull) < 0x7FF0000000000000ull) &
+                         ((ib & 0x7FFFFFFFFFFFFFFFull) < 0x7FF0000000000000ull);
+        if (!fin) return false;
+        const double a = __longlong_as_double((long long)ia), b = __longlong_as_double((long long)ib);
+        const double d = fabs(__dsub_rn(a, b));
+        const double m = fmax(fabs(a), fabs(b));
+        return (d <= ta) | (d <= __dmul_rn(tr, m));
+    }
+    static __device__ __forceinline__ bool eq(const P &x, const P &y, Ctx c)
+    {
+        return x.bits == y.bits || eq_slow(x.bits, y.bits, c.a, c.r);
+    }
+    static __device__ __forceinline__ V get(const uint4 &v, int e)
+    {
+        return e == 0 ? ((V)v.y << 32 | v.x) : ((V)v.w << 32 | v.z);
+    }
+    static __device__ __forceinline__ void set(uint4 &v, int e, V x)
+    {
+        if (e == 0) { v.x = (uint32_t)x; v.y = (uint32_t)(x >> 32); }
+        else        { v.z = (uint32_t)x; v.w = (uint32_t)(x >> 32); }
+    }
+};
+
+template <typename VV, int S, int PER>
+struct ElemBits {
+    using V = VV;
+    static constexpr int kSize = S;
+    static constexpr bool kBitsFirst = false;
+    struct Ctx {};
+    struct P { V bits; };
+    static __device__ __forceinline__ Ctx ctx(double, double) { return {}; }
+    static __device__ __forceinline__ P prep(V x, Ctx) { return {x}; }
+    static __device__ __forceinline__ bool eq(const P &x, const P &y, Ctx) { return x.bits == y.bits; }
+};
+
+template <> struct Elem<K_B4> : ElemBits<uint32_t, 4, 4> {
+    static __device__ __forceinline__ V get(const uint4 &v, int e) { return (&v.x)[e]; }
+    static __device__ __forceinline__ void set(uint4 &v, int e, V x) { (&v.x)[e] = x; }
+};
+
+template <> struct Elem<K_B8> : ElemBits<unsigned long long, 8, 2> {
+    static __device__ __forceinline__ V get(const uint4 &v, int e) { return Elem<K_F64>::get(v, e); }
+    static __device__ __forceinline__ void set(uint4 &v, int e, V x) { Elem<K_F64>::set(v, e, x); }
+};
+
+template <> struct Elem<K_B1> : ElemBits<uint32_t, 1, 16> {   // one byte, zero-extended
+    static __device__ __forceinline__ V get(const uint4 &v, int e) { return ((&v.x)[e >> 2] >> (8 * (e & 3))) & 0xFFu; }
+    static __device__ __forceinline__ void set(uint4 &v, int e, V x)
+    {
+        uint32_t &w = (&v.x)[e >> 2];
+        const int s = 8 * (e & 3);
+        w = (w & ~(0xFFu << s)) | (x << s);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The vote of one element, exact form.  E[r] is the set (bit mask) of
+// replicas equal to x_r, self included, so the support is popc(E[r]); the
+// first maximum wins.  Returns the winner's bits in y and in m the mismatch
+// mask (bit r: x_r is not equal to the winner) with bit R set when there is no
+// majority.
+// ---------------------------------------------------------------------------
+template <int K, int R>
+__device__ __forceinline__ void vote_elem(const typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
+                                          typename Elem<K>::V &y, uint32_t &m)
+{
+    using E = Elem<K>;
+    typename E::P p[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r] = E::prep(x[r], c);
+    uint32_t Em[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Em[r] = 1u << r;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = r + 1; q < R; ++q) {
+            const bool e = E::eq(p[r], p[q], c);
+            Em[r] |= e ? (1u << q) : 0u;
+            Em[q] |= e ? (1u << r) : 0u;
+        }
+    int best = __popc(Em[0]);
+    uint32_t Ew = Em[0];
+    y = x[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const int s = __popc(Em[r]);
+        const bool better = s > best;
+        best = better ? s : best;
+        Ew = better ? Em[r] : Ew;
+        y = better ? x[r] : y;
+    }
+    m = (~Ew & ((1u << R) - 1u)) | ((2 * best > R) ? 0u : (1u << R));
+}
+
+// Fast form: the winner's bits, and `flag` raised whenever the element may
+// have a mismatch or no majority (a superset; the exact statistics are then
+// recomputed with vote_elem).
+template <int K, int R>
+__device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
+                                          typename Elem<K>::V &y, bool &flag)
+{
+    using E = Elem<K>;
+    if constexpr (E::kBitsFirst) {
+        bool same = true;
+#pragma unroll
+        for (int r = 1; r < R; ++r) same &= (x[r] == x[0]);
+        if (same) {
+            y = x[0];
+        } else {
+            uint32_t m;
+            vote_elem<K, R>(x, c, y, m);
+            flag |= (m != 0);
+        }
+    } else if constexpr (R == 3) {
+        // supports (1+e01+e02, 1+e01+e12, 1+e02+e12): replica 1 wins iff
+        // e12 and not e02; replica 2 iff e02, e12 and not e01; else replica 0.
+        // A mismatch or a missing majority needs not (e01 and e02), except in
+        // the non-transitive cases, which only raise the flag.
+        const typename E::P p0 = E::prep(x[0], c), p1 = E::prep(x[1], c), p2 = E::prep(x[2], c);
+        const bool e01 = E::eq(p0, p1, c), e02 = E::eq(p0, p2, c), e12 = E::eq(p1, p2, c);
+        const bool w1 = e12 & !e02;
+        const bool w2 = e02 & e12 & !e01;
+        y = w2 ? x[2] : (w1 ? x[1] : x[0]);
+        flag |= !(e01 & e02);
+    } else {
+        uint32_t m;
+        vote_elem<K, R>(x, c, y, m);
+        flag |= (m != 0);
+    }
+}
+
+// Per-lane statistics: counts and first indices for the R replicas and, at
+// index R, for elements without a majority.
+template <int R>
+struct LaneStats {
+    unsigned long long cnt[R + 1];
+    unsigned long long first[R + 1];
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int r = 0; r <= R; ++r) { cnt[r] = 0; first[r] = kNone; }
+    }
+    __device__ __forceinline__ void add_one(uint32_t m, unsigned long long idx)
+    {
+#pragma unroll
+        for (int r = 0; r <= R; ++r)
+            if ((m >> r) & 1u) {
+                cnt[r] += 1;
+                first[r] = first[r] < idx ? first[r] : idx;
+            }
+    }
+    __device__ __forceinline__ void merge(const LaneStats &o)
+    {
+#pragma unroll
+        for (int r = 0; r <= R; ++r) {
+            cnt[r] += o.cnt[r];
+            first[r] = o.first[r] < first[r] ? o.first[r] : first[r];
+        }
+    }
+    // Warp-reduce and add into the task's ft_stats (one atomic per non-empty
+    // quantity per warp).
+    __device__ __forceinline__ void flush(ft_stats *s, int lane)
+    {
+#pragma unroll
+        for (int r = 0; r <= R; ++r) {
+            unsigned long long c = cnt[r], f = first[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+                const unsigned long long g = __shfl_xor_sync(0xFFFFFFFFu, f, o);
+                f = g < f ? g : f;
+            }
+            if (lane == 0) {
+                unsigned long long *pc = r < R ? reinterpret_cast<unsigned long long *>(&s->mismatch[r])
+                                               : reinterpret_cast<unsigned long long *>(&s->no_majority);
+                unsigned long long *pf = r < R ? reinterpret_cast<unsigned long long *>(&s->first_mismatch[r])
+                                               : reinterpret_cast<unsigned long long *>(&s->first_no_majority);
+                if (c) atomicAdd(pc, c);
+                if (f != kNone) atomicMin(pf, f);
+            }
+        }
+    }
+};
+
+// Statistics of one task are reset to (0, -1) before its vote.
+__device__ __forceinline__ void reset_stats(ft_stats *s, int i)
+{
+    if (i < FT_MAX_R) { s->mismatch[i] = 0; s->first_mismatch[i] = -1; }
+    if (i == FT_MAX_R) { s->no_majority = 0; s->first_no_majority = -1; }
+}
+
+// Arguments of one vote as the kernels see them.
+struct TaskArgs {
+    const uint8_t *rep[FT_MAX_R];
+    uint8_t *out;
+    uint32_t *crc;          // may be null
+    ft_stats *stats;
+    unsigned long long n;   // elements
+    unsigned long long nfull;   // full 4 KiB blocks
+    uint32_t tail_bytes;    // bytes of the partial last block (0 = none)
+    int32_t R;
+    int32_t kind;
+    int32_t pad_;
+    double abs_tol, rel_tol;
+};
+
+template <int K>
+__device__ __forceinline__ typename Elem<K>::V load_elem(const uint8_t *p)
+{
+    if constexpr (Elem<K>::kSize == 8) return *reinterpret_cast<const unsigned long long *>(p);
+    else if constexpr (Elem<K>::kSize == 4) return *reinterpret_cast<const uint32_t *>(p);
+    else return *p;
+}
+
+template <int K>
+__device__ __forceinline__ void store_elem(uint8_t *p, typename Elem<K>::V v)
+{
+    if constexpr (Elem<K>::kSize == 8) *reinterpret_cast<unsigned long long *>(p) = v;
+    else if constexpr (Elem<K>::kSize == 4) *reinterpret_cast<uint32_t *>(p) = v;
+    else *p = (uint8_t)v;
+}
+
+// Exact statistics of the elements of lane `lane`'s vectors j0 .. j0+JB-1 of
+// block b, recomputed from global memory (rare path).
+template <int K, int R, int JB>
+__device__ __noinline__ void exact_stats(const TaskArgs &a, unsigned long long b, int j0, int lane, LaneStats<R> &st)
+{
+    using E = Elem<K>;
+    constexpr int kPerVec = 16 / E::kSize;
+    constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
+    const typename E::Ctx c = E::ctx(a.abs_tol, a.rel_tol);
+    for (int jj = 0; jj < JB; ++jj) {
+        const unsigned long long vi = (unsigned long long)(lane + 32 * (j0 + jj));
+        for (int e = 0; e < kPerVec; ++e) {
+            const unsigned long long off = b * kBlockBytes + vi * 16 + (unsigned long long)e * E::kSize;
+            typename E::V x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = load_elem<K>(a.rep[r] + off);
+            typename E::V y;
+            uint32_t m;
+            vote_elem<K, R>(x, c, y, m);
+            if (m) st.add_one(m, b * kEpb + vi * kPerVec + e);
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ const uint8_t *rep_for_lane(const TaskArgs &a, int lane)
+{
+    const uint8_t *p = a.rep[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) p = (lane == r) ? a.rep[r] : p;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// One full 4 KiB block of one task, voted and digested by one warp.  Lanes
+// 0..R-1 first prefetch the warp's next block (b_next, if any) into L2.
+// ---------------------------------------------------------------------------
+template <int K, int R>
+__device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long long b, unsigned long long b_next,
+                                                uint4 *tile, const uint32_t *s_crc, const uint32_t *s_comb,
+                                                const CrcLane &L, LaneStats<R> &st, int lane)
+{
+    using E = Elem<K>;
+    using V = typename E::V;
+    constexpr int kPerVec = 16 / E::kSize;
+    constexpr int JB = (R <= 2) ? 8 : (R <= 4 ? 4 : 2);      // vectors per lane per sub-batch
+    const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
+    const unsigned long long boff = b * kBlockBytes;
+    if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);
+
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0 += JB) {
+        uint4 v[R][JB];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj)
+                v[r][jj] = __ldcs(reinterpret_cast<const uint4 *>(a.rep[r] + boff) + lane + 32 * (j0 + jj));
+        bool flag = false;
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            uint4 yv = v[0][jj];
+#pragma unroll
+            for (int e = 0; e < kPerVec; ++e) {
+                V x[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[r] = E::get(v[r][jj], e);
+                V y;
+                vote_fast<K, R>(x, ctx, y, flag);
+                E::set(yv, e, y);
+            }
+            const int vi = lane + 32 * (j0 + jj);
+            __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
+            tile[tile_index(vi)] = yv;
+        }
+        if (flag) exact_stats<K, R, JB>(a, b, j0, lane, st);
+    }
+    __syncwarp();
+    const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);
+    if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
+    __syncwarp();
+}
+
+// The partial last block (a.tail_bytes bytes), element by element.
+template <int K, int R>
+__device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long long b, uint4 *tile,
+                                             const uint32_t *s_crc, LaneStats<R> &st, int lane)
+{
+    using E = Elem<K>;
+    using V = typename E::V;
+    constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
+    const typename E::Ctx c = E::ctx(a.abs_tol, a.rel_tol);
+    const uint32_t len = a.tail_bytes;
+    const unsigned long long boff = b * kBlockBytes;
+    const uint32_t e0 = (128u * lane) / E::kSize;
+    const uint32_t e1 = min(128u * (lane + 1), len) / E::kSize;
+    uint8_t *tb = reinterpret_cast<uint8_t *>(tile);
+    for (uint32_t e = e0; e < e1; ++e) {
+        const unsigned long long off = boff + (unsigned long long)e * E::kSize;
+        V x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = load_elem<K>(a.rep[r] + off);
+        V y;
+        uint32_t m;
+        vote_elem<K, R>(x, c, y, m);
+        store_elem<K>(a.out + off, y);
+        const uint32_t bo = e * E::kSize;
+        store_elem<K>(tb + tile_index(bo >> 4) * 16 + (bo & 15u), y);
+        if (m) st.add_one(m, b * kEpb + e);
+    }
+    __syncwarp();
+    const uint32_t raw = tile_crc_partial(tile, s_crc, len, lane);
+    if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ gf_mul(0xFFFFFFFFu, gf_xpow8(len)));
+    __syncwarp();
+}
+
+}  // namespace ftv

@@ -1,0 +1,59 @@
+// runtime.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <atomic>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "ftvote.h"
+
+namespace ftv {
+
+struct TaskArgs;
+
+// Optional launch override of the single-task voter (tests and tuning).
+struct VoteLaunch {
+    int ctas_per_sm;   // 0 = occupancy limit
+};
+
+extern std::atomic<unsigned long long> g_launches;
+extern thread_local int g_last_cuda;
+
+int cuda_fail(cudaError_t e);
+int check_launch(int nlaunch);
+int occupancy(const void *fn, int threads, size_t smem, int *sms, int *per_sm);
+size_t dtype_size(int dtype);
+int dtype_kind(int dtype);
+int validate_desc(const ft_vote_desc *d);
+TaskArgs make_task_args(const ft_vote_desc *d);
+int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
+int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg);
+
+// One (element kind, R) group of a batch, as the batched kernel sees it.
+// tasks[t] for t in [t0, t1) belong to the group; the group's work is split
+// into total_tiles tiles of tile_blocks 4 KiB blocks; tile_task[g] is the task
+// of the group's tile g and tile_first[t] the group tile where task t starts.
+struct GroupDev {
+    const TaskArgs *tasks;
+    const uint32_t *tile_task;
+    const unsigned long long *tile_first;
+    unsigned long long total_tiles;
+    unsigned long long *counter;   // tile dispenser, zeroed by the reset kernel
+    int32_t tile_blocks;
+    int32_t kind;
+    int32_t R;
+    int32_t pad_;
+};
+
+// Reset the statistics of tasks[0..ntasks) and zero ncounters counters.
+int launch_batch_reset(const TaskArgs *tasks, int ntasks, unsigned long long *counters, int ncounters,
+                       cudaStream_t s);
+// Launch the persistent batched voter for one group.
+int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s);
+// Resident CTAs per SM of the batched kernel for (kind, R) and the SM count.
+int group_occupancy(int kind, int R, int *sms, int *per_sm);
+// Copy stats of tasks[i] to user[i] where user[i] is not null (server).
+int launch_stats_scatter(const ft_stats *src, ft_stats *const *dst, int n, cudaStream_t s);
+int digest(const void *buf, unsigned long long nbytes, uint32_t block_bytes, uint32_t *out, cudaStream_t s);
+
+}  // namespace ftv

@@ -1,0 +1,379 @@
+// server.cpp -- the serving form of the voter: continuous batching of vote
+// requests (ft_server_create / ft_submit / ft_poll).
+//
+// Requests are admitted against a device-memory budget: each one holds
+// (R+1) * n * sizeof(dtype) bytes of resident replicas and output until its
+// result is collected.  A worker thread packs the admitted requests that are
+// waiting into the next batch (up to max_slots), lays the batch out for the
+// persistent batched kernels and launches it on one of `streams` CUDA
+// streams, so that a new batch starts while earlier ones are still on the
+// device.  A host callback enqueued after each batch marks its requests done;
+// ft_poll waits for that with a bound, as the paper's runtime bounds the wait
+// for a task by a timeout (Sec. IV.C).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "batched.h"
+#include "ftvote.h"
+#include "runtime.h"
+
+namespace {
+
+double now_us()
+{
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    ftv::TaskArgs args;
+    ft_stats *user_stats = nullptr;
+    unsigned long long bytes = 0;
+    double submit_us = 0, done_us = 0;
+    int status = FT_EAGAIN;
+    bool done = false;
+    ft_stats result;
+};
+
+struct Slot;
+
+struct Callback {
+    ft_server *srv;
+    int slot;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    uint8_t *dev = nullptr;            // batch layout (device)
+    size_t dev_cap = 0;
+    uint8_t *host = nullptr;           // batch layout staging (pinned)
+    size_t host_cap = 0;
+    ft_stats *dev_stats = nullptr;     // per request of the batch
+    ft_stats *host_stats = nullptr;    // pinned copy read by the callback
+    ft_stats **dev_user = nullptr;     // caller stats pointers (scatter targets)
+    ft_stats **host_user = nullptr;    // pinned
+    int cap = 0;                       // requests per batch
+    bool busy = false;
+    int status = FT_OK;
+    std::vector<unsigned long long> tickets;
+    ftv::BatchLayout layout;
+    std::vector<ftv::GroupDev> gd;
+    Callback cb;
+};
+
+}  // namespace
+
+struct ft_server {
+    ft_server_config cfg{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work;   // worker: new requests, a free slot, stop
+    std::condition_variable cv_done;   // pollers: a request completed
+    std::deque<unsigned long long> pending;
+    std::unordered_map<unsigned long long, Request> reqs;
+    unsigned long long next_ticket = 1;
+    unsigned long long inflight_bytes = 0;
+    int inflight = 0;
+    bool stop = false;
+    bool paused = false;
+    std::vector<Slot> slots;
+    std::thread worker;
+};
+
+namespace {
+
+void CUDART_CB batch_done(void *p)
+{
+    Callback *cb = static_cast<Callback *>(p);
+    ft_server *s = cb->srv;
+    const double t = now_us();
+    std::lock_guard<std::mutex> lk(s->mu);
+    Slot &sl = s->slots[cb->slot];
+    for (size_t i = 0; i < sl.tickets.size(); ++i) {
+        auto it = s->reqs.find(sl.tickets[i]);
+        if (it == s->reqs.end()) continue;
+        Request &r = it->second;
+        r.result = sl.host_stats[i];
+        r.status = sl.status;
+        r.done = true;
+        r.done_us = t;
+    }
+    sl.tickets.clear();
+    sl.busy = false;
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
+{
+    cudaError_t e;
+    if (layout_bytes > sl.dev_cap) {
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.host) cudaFreeHost(sl.host);
+        sl.dev = sl.host = nullptr;
+        sl.dev_cap = sl.host_cap = 0;
+        const size_t cap = layout_bytes + layout_bytes / 2;
+        if ((e = cudaMalloc(&sl.dev, cap)) != cudaSuccess) return ftv::cuda_fail(e);
+        if ((e = cudaMallocHost(&sl.host, cap)) != cudaSuccess) return ftv::cuda_fail(e);
+        sl.dev_cap = sl.host_cap = cap;
+    }
+    if (nreq > sl.cap) {
+        if (sl.dev_stats) cudaFree(sl.dev_stats);
+        if (sl.host_stats) cudaFreeHost(sl.host_stats);
+        if (sl.dev_user) cudaFree(sl.dev_user);
+        if (sl.host_user) cudaFreeHost(sl.host_user);
+        sl.dev_stats = nullptr;
+        sl.host_stats = nullptr;
+        sl.dev_user = sl.host_user = nullptr;
+        sl.cap = 0;
+        if ((e = cudaMalloc(&sl.dev_stats, sizeof(ft_stats) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
+        if ((e = cudaMallocHost(&sl.host_stats, sizeof(ft_stats) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
+        if ((e = cudaMalloc(&sl.dev_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
+        if ((e = cudaMallocHost(&sl.host_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
+        sl.cap = nreq;
+    }
+    return FT_OK;
+}
+
+// Launch the requests `tickets` as one batch on slot `si` (lock not held).
+int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any_user)
+{
+    Slot &sl = s->slots[si];
+    const int n = (int)args.size();
+    for (int i = 0; i < n; ++i) args[i].stats = nullptr;   // set below, after growing
+    int rc = FT_OK;
+    sl.layout.build(args, s->cfg.tile_blocks);
+    rc = grow_slot(sl, sl.layout.device_bytes(), n);
+    if (rc != FT_OK) return rc;
+    // statistics of request i go to dev_stats[i]; the layout orders tasks by
+    // (kind, R), so patch through its index map
+    for (size_t t = 0; t < sl.layout.tasks.size(); ++t) sl.layout.tasks[t].stats = sl.dev_stats + sl.layout.user_index[t];
+    const size_t bytes = sl.layout.device_bytes();
+    sl.layout.pack(sl.host, sl.dev, sl.gd);
+    cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, sl.stream);
+    if (e != cudaSuccess) return ftv::cuda_fail(e);
+    if ((rc = ftv::launch_batch(sl.layout, sl.gd, 0, sl.stream)) != FT_OK) return rc;
+    if (any_user) {
+        if ((e = cudaMemcpyAsync(sl.dev_user, sl.host_user, sizeof(ft_stats *) * n, cudaMemcpyHostToDevice,
+                                 sl.stream)) != cudaSuccess)
+            return ftv::cuda_fail(e);
+        if ((rc = ftv::launch_stats_scatter(sl.dev_stats, sl.dev_user, n, sl.stream)) != FT_OK) return rc;
+    }
+    if ((e = cudaMemcpyAsync(sl.host_stats, sl.dev_stats, sizeof(ft_stats) * n, cudaMemcpyDeviceToHost,
+                             sl.stream)) != cudaSuccess)
+        return ftv::cuda_fail(e);
+    return FT_OK;
+}
+
+void worker_main(ft_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        int free_slot = -1;
+        for (size_t i = 0; i < s->slots.size(); ++i)
+            if (!s->slots[i].busy) { free_slot = (int)i; break; }
+        bool any_busy = false;
+        for (auto &sl : s->slots) any_busy |= sl.busy;
+        if (s->stop && !any_busy) break;
+        if (s->stop || s->paused || s->pending.empty() || free_slot < 0) {
+            s->cv_work.wait(lk);
+            continue;
+        }
+        // take up to max_slots waiting requests (FIFO) into this slot
+        Slot &sl = s->slots[free_slot];
+        std::vector<ftv::TaskArgs> args;
+        sl.tickets.clear();
+        bool any_user = false;
+        while (!s->pending.empty() && (int)args.size() < s->cfg.max_slots) {
+            const unsigned long long tk = s->pending.front();
+            s->pending.pop_front();
+            auto it = s->reqs.find(tk);
+            if (it == s->reqs.end()) continue;
+            args.push_back(it->second.args);
+            sl.tickets.push_back(tk);
+            any_user |= it->second.user_stats != nullptr;
+        }
+        if (args.empty()) continue;
+        sl.busy = true;
+        std::vector<ft_stats *> users(args.size());
+        for (size_t i = 0; i < args.size(); ++i) users[i] = s->reqs[sl.tickets[i]].user_stats;
+        lk.unlock();
+        int rc = FT_OK;
+        if (any_user) {
+            rc = grow_slot(sl, 0, (int)args.size());
+            if (rc == FT_OK) std::memcpy(sl.host_user, users.data(), sizeof(ft_stats *) * users.size());
+        }
+        if (rc == FT_OK) rc = launch_slot(s, free_slot, args, any_user);
+        sl.status = rc;
+        sl.cb = Callback{s, free_slot};
+        cudaError_t e = cudaLaunchHostFunc(sl.stream, batch_done, &sl.cb);
+        lk.lock();
+        if (e != cudaSuccess) {
+            // the completion callback could not be queued: finish the batch here
+            lk.unlock();
+            cudaStreamSynchronize(sl.stream);
+            sl.status = ftv::cuda_fail(e);
+            batch_done(&sl.cb);
+            lk.lock();
+        }
+    }
+}
+
+void free_server(ft_server *s)
+{
+    for (auto &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.dev_stats) cudaFree(sl.dev_stats);
+        if (sl.host_stats) cudaFreeHost(sl.host_stats);
+        if (sl.dev_user) cudaFree(sl.dev_user);
+        if (sl.host_user) cudaFreeHost(sl.host_user);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ft_server_create(ft_server **out, const ft_server_config *cfg)
+{
+    if (!out || !cfg) return FT_EINVAL;
+    *out = nullptr;
+    if (cfg->mem_budget_bytes == 0 || cfg->max_slots < 1 || cfg->max_slots > 65536 || cfg->streams < 1 ||
+        cfg->streams > 8 || cfg->tile_blocks < 0 || cfg->tile_blocks > 64 || cfg->max_inflight < 0)
+        return FT_EINVAL;
+    ft_server *s = new (std::nothrow) ft_server();
+    if (!s) return FT_ENOMEM;
+    s->cfg = *cfg;
+    if (s->cfg.tile_blocks == 0) s->cfg.tile_blocks = 8;
+    if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 65536;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return ftv::cuda_fail(e);
+    }
+    s->slots.resize(cfg->streams);
+    int rc = FT_OK;
+    // size each slot for a batch that fills the whole budget
+    const unsigned long long tiles = cfg->mem_budget_bytes / (2ull * 4096ull * s->cfg.tile_blocks) + cfg->max_slots;
+    const size_t guess = sizeof(ftv::TaskArgs) * cfg->max_slots + 8ull * cfg->max_slots + 4ull * tiles + 4096;
+    for (auto &sl : s->slots) {
+        if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            rc = ftv::cuda_fail(e);
+            break;
+        }
+        if ((rc = grow_slot(sl, guess, std::min(cfg->max_slots, 4096))) != FT_OK) break;
+    }
+    if (rc != FT_OK) {
+        free_server(s);
+        return rc == FT_ECUDA && ftv::g_last_cuda == cudaErrorMemoryAllocation ? FT_ENOMEM : rc;
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return FT_OK;
+}
+
+int ft_submit(ft_server *s, const ft_vote_desc *desc, uint64_t *ticket)
+{
+    if (!s || !desc || !ticket) return FT_EINVAL;
+    // the server supplies the statistics buffer when the caller gives none
+    ft_vote_desc d = *desc;
+    ft_stats dummy;
+    const bool user = d.stats != nullptr;
+    if (!user) d.stats = &dummy;
+    int rc = ftv::validate_desc(&d);
+    if (rc != FT_OK) return rc;
+    const unsigned long long bytes = (unsigned long long)(d.R + 1) * d.n * ftv::dtype_size(d.dtype);
+    if (bytes > s->cfg.mem_budget_bytes) return FT_EINVAL;   // can never be admitted
+    Request r;
+    r.args = ftv::make_task_args(&d);
+    r.user_stats = user ? desc->stats : nullptr;
+    r.bytes = bytes;
+    r.submit_us = now_us();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return FT_EINVAL;
+    if (s->inflight_bytes + bytes > s->cfg.mem_budget_bytes || s->inflight >= s->cfg.max_inflight) return FT_EAGAIN;
+    const unsigned long long t = s->next_ticket++;
+    s->reqs.emplace(t, r);
+    s->pending.push_back(t);
+    s->inflight_bytes += bytes;
+    s->inflight += 1;
+    *ticket = t;
+    s->cv_work.notify_one();
+    return FT_OK;
+}
+
+int ft_poll(ft_server *s, uint64_t ticket, int64_t timeout_us, ft_result *res)
+{
+    if (!s) return FT_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return FT_ENOTFOUND;
+    if (!it->second.done) {
+        auto ready = [&] {
+            auto j = s->reqs.find(ticket);
+            return j == s->reqs.end() || j->second.done;
+        };
+        if (timeout_us < 0) {
+            s->cv_done.wait(lk, ready);
+        } else if (timeout_us > 0) {
+            s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+        }
+        it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return FT_ENOTFOUND;
+        if (!it->second.done) return FT_ETIMEDOUT;
+    }
+    Request &r = it->second;
+    if (res) {
+        res->status = r.status;
+        res->R = r.args.R;
+        res->n = r.args.n;
+        res->stats = r.result;
+        res->submit_us = r.submit_us;
+        res->done_us = r.done_us;
+    }
+    s->inflight_bytes -= r.bytes;
+    s->inflight -= 1;
+    s->reqs.erase(it);
+    return FT_OK;
+}
+
+int ft_server_pause(ft_server *s, int32_t paused)
+{
+    if (!s) return FT_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+    s->cv_work.notify_all();
+    return FT_OK;
+}
+
+int ft_server_destroy(ft_server *s)
+{
+    if (!s) return FT_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->pending.clear();
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    free_server(s);
+    return FT_OK;
+}
+
+double ft_clock_us(void) { return now_us(); }
+
+}  // extern "C"

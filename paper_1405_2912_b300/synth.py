@@ -244,7 +244,7 @@ def task_problem(spec: TaskSpec, config_id: int = 4, flip_rate: float = 1e-4,
         base = lognormal(rng, spec.n, spec.dtype)
     reps = [base.copy() for _ in range(spec.R)]
     truth = {"clean": base}
-    if ulp_frac > 0 and spec.dtype != "i32":
+    if ulp_frac > 0 and spec.dtype in ("f32", "f64"):
         idx = np.flatnonzero(rng.random(spec.n) < ulp_frac)
         ulp_perturb(reps[1], idx, rng.integers(1, 3, size=idx.size))
     if spec.faulty:

@@ -1,0 +1,145 @@
+"""The serving form (ft_server_create / ft_submit / ft_poll): continuous
+batching gives every request the same bit-exact result alone and in the mix;
+admission follows the device-memory budget; waits are bounded (a request held
+back on the host times out and completes once released); unknown tickets are
+reported.  Failures are made on the host only."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1405_2912_b300 import synth
+
+from _gpu import DevTask, assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+def _server(budget, max_slots=16, streams=2, tile=8, max_inflight=0):
+    from paper_1405_2912_b300 import ftvote as fv
+    cfg = fv.ft_server_config(budget, max_slots, streams, tile, max_inflight)
+    srv = ctypes.c_void_p()
+    fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
+    return srv
+
+
+def _requests(k=40, seed=2):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(k):
+        n = int(np.exp(rng.uniform(np.log(4096), np.log(300_000))))
+        specs.append(synth.TaskSpec(n + int(rng.integers(0, 5)), ["f32", "f64"][i % 2], [3, 5][(i // 2) % 2],
+                                    bool(i % 4 == 0), 9000 + i))
+    return [synth.task_problem(s, config_id=5, ulp_frac=0.05, flip_rate=1e-3) for s in specs]
+
+
+def _stats_dict(st, R):
+    return {"mismatch": np.array(list(st.mismatch)[:R], dtype=np.uint64),
+            "first_mismatch": np.array(list(st.first_mismatch)[:R], dtype=np.int64),
+            "no_majority": int(st.no_majority), "first_no_majority": int(st.first_no_majority)}
+
+
+def test_same_alone_and_in_the_mix():
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    probs = _requests()
+    alone = [DevTask(p) for p in probs]
+    for t in alone:
+        fv.check(fv.ft_vote(ctypes.byref(t.desc), fv.stream_handle()), "ft_vote")
+    torch.cuda.synchronize()
+    alone_res = [t.result() for t in alone]
+    mixed = [DevTask(p) for p in probs]
+    srv = _server(budget=1 << 34)
+    try:
+        tickets = []
+        for i, t in enumerate(mixed):
+            d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+            if i % 3 == 0:
+                d.stats = None          # statistics only through ft_result
+            tk = ctypes.c_uint64()
+            fv.check(fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)), "ft_submit")
+            tickets.append(tk.value)
+        results = []
+        for tk in tickets:
+            r = fv.ft_result()
+            fv.check(fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)), "ft_poll")
+            assert r.status == fv.FT_OK and r.done_us >= r.submit_us
+            results.append(r)
+    finally:
+        fv.ft_server_destroy(srv)
+    torch.cuda.synchronize()
+    for i, (p, t, a, r) in enumerate(zip(probs, mixed, alone_res, results)):
+        got = t.result()
+        sd = _stats_dict(r.stats, p.R)
+        if i % 3 == 0:
+            got.update(sd)
+            got["raw_stats"] = a["raw_stats"]
+        else:
+            for k, v in sd.items():
+                assert np.array_equal(np.asarray(got[k]), np.asarray(v)), (i, k)
+        assert_same(got, a, p.R)
+        if i % 7 == 0:
+            assert_same(got, oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
+
+
+def test_admission_by_budget_and_slots():
+    from paper_1405_2912_b300 import ftvote as fv
+    probs = _requests(k=3, seed=5)
+    tasks = [DevTask(p) for p in probs]
+    need = [(p.R + 1) * p.n * p.itemsize for p in probs]
+    srv = _server(budget=need[0] + need[1])
+    try:
+        fv.ft_server_pause(srv, 1)
+        t = [ctypes.c_uint64() for _ in range(3)]
+        assert fv.ft_submit(srv, ctypes.byref(tasks[0].desc), ctypes.byref(t[0])) == fv.FT_OK
+        assert fv.ft_submit(srv, ctypes.byref(tasks[1].desc), ctypes.byref(t[1])) == fv.FT_OK
+        # over budget: refused, nothing kept
+        assert fv.ft_submit(srv, ctypes.byref(tasks[2].desc), ctypes.byref(t[2])) == fv.FT_EAGAIN
+        fv.ft_server_pause(srv, 0)
+        r = fv.ft_result()
+        assert fv.ft_poll(srv, t[0].value, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+        # budget released by collecting the result
+        assert fv.ft_submit(srv, ctypes.byref(tasks[2].desc), ctypes.byref(t[2])) == fv.FT_OK
+        for k in (1, 2):
+            assert fv.ft_poll(srv, t[k].value, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+        # a request larger than the whole budget can never be admitted
+        big = fv.ft_vote_desc.from_buffer_copy(tasks[0].desc)
+        big.n = 1 << 40
+        assert fv.ft_submit(srv, ctypes.byref(big), ctypes.byref(t[0])) == fv.FT_EINVAL
+    finally:
+        fv.ft_server_destroy(srv)
+    srv = _server(budget=1 << 34, max_inflight=1)
+    try:
+        fv.ft_server_pause(srv, 1)
+        assert fv.ft_submit(srv, ctypes.byref(tasks[0].desc), ctypes.byref(t[0])) == fv.FT_OK
+        assert fv.ft_submit(srv, ctypes.byref(tasks[1].desc), ctypes.byref(t[1])) == fv.FT_EAGAIN
+        fv.ft_server_pause(srv, 0)
+        assert fv.ft_poll(srv, t[0].value, -1, ctypes.byref(r)) == fv.FT_OK
+    finally:
+        fv.ft_server_destroy(srv)
+
+
+def test_bounded_wait_and_unknown_tickets():
+    from paper_1405_2912_b300 import ftvote as fv
+    p = _requests(k=1, seed=7)[0]
+    t = DevTask(p)
+    srv = _server(budget=1 << 32)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tk = ctypes.c_uint64()
+        assert fv.ft_submit(srv, ctypes.byref(t.desc), ctypes.byref(tk)) == fv.FT_OK
+        r = fv.ft_result()
+        t0 = time.monotonic()
+        assert fv.ft_poll(srv, tk.value, 20_000, ctypes.byref(r)) == fv.FT_ETIMEDOUT
+        assert time.monotonic() - t0 >= 0.015
+        assert fv.ft_poll(srv, tk.value, 0, ctypes.byref(r)) == fv.FT_ETIMEDOUT
+        fv.ft_server_pause(srv, 0)
+        assert fv.ft_poll(srv, tk.value, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+        assert fv.ft_poll(srv, tk.value, 0, ctypes.byref(r)) == fv.FT_ENOTFOUND
+        assert fv.ft_poll(srv, 123456789, 0, ctypes.byref(r)) == fv.FT_ENOTFOUND
+        ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        assert list(r.stats.mismatch)[:p.R] == [int(x) for x in ref["mismatch"]]
+    finally:
+        fv.ft_server_destroy(srv)

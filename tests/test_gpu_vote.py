@@ -1,0 +1,119 @@
+"""GPU parity of ft_vote (the CUDA voter, called through the C ABI) against the
+CPU oracle, element by element and bit-exactly: voted values, per-4-KiB-block
+CRC32C, per-replica mismatch counts and first indices, no-majority count and
+first index.  Sizes span many 4 KiB blocks and ragged tails; the workloads are
+the seeded generators of the five voter workloads, scaled down, plus the full
+256M-element f32 workload in the launch configuration that bench.py times."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1405_2912_b300 import synth
+
+from _gpu import assert_same, gpu_vote
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 3, 5, 31, 1023, 1024, 1025, 2048 + 3, 4097, 12345, 65536 + 77, 300_001]
+
+
+def _special(dtype, rng, n):
+    if dtype == "f32":
+        pool = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-45, -1e-45, 3.4e38, -3.4e38, 1.0,
+                         1.0000001, 0.9999999], dtype=np.float32)
+    else:
+        pool = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, 1.7e308, 1.0, 1.0 + 2e-16],
+                        dtype=np.float64)
+    return pool[rng.integers(0, pool.size, size=n)]
+
+
+def _random_problem(dtype, R, n, seed):
+    """Replicas with ULP noise, bit flips, specials and tie patterns."""
+    rng = np.random.default_rng(seed)
+    t = oracle.NP_OF[dtype]
+    if dtype in ("f32", "f64"):
+        base = synth.lognormal(rng, n, dtype)
+        sp = rng.random(n) < 0.02
+        base[sp] = _special(dtype, rng, int(sp.sum()))
+        tol = synth.TOL[dtype]
+    else:
+        info = np.iinfo(t)
+        base = rng.integers(info.min, info.max, size=n, dtype=t, endpoint=True)
+        tol = (0.0, 0.0)
+    reps = [base.copy() for _ in range(R)]
+    for r in range(R):
+        if dtype in ("f32", "f64") and n:
+            idx = np.flatnonzero(rng.random(n) < 0.1)
+            synth.ulp_perturb(reps[r], idx, rng.integers(1, 6, size=idx.size))
+        idx = np.flatnonzero(rng.random(n) < 0.03)
+        synth.bit_flip(reps[r], idx, rng.integers(0, 8 * reps[r].dtype.itemsize, size=idx.size))
+        # occasional whole-element replacement from another replica: ties and clusters
+        idx = np.flatnonzero(rng.random(n) < 0.05)
+        src = reps[int(rng.integers(0, R))]
+        reps[r][idx] = src[idx]
+    return reps, tol
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "i32", "u32", "i64", "u64", "u8"])
+@pytest.mark.parametrize("R", [2, 3, 4, 5, 6, 7, 8])
+def test_random_all_types(dtype, R):
+    for k, n in enumerate(SIZES if R in (3, 5) else SIZES[::3]):
+        reps, tol = _random_problem(dtype, R, n, seed=1000 * R + k)
+        ref = oracle.vote(reps, dtype, *tol)
+        got = gpu_vote(reps, dtype, *tol)
+        assert_same(got, ref, R)
+
+
+def test_empty_vote_resets_stats():
+    reps = [np.zeros(0, dtype=np.float32)] * 3
+    got = gpu_vote(reps, "f32", 1e-6, 1e-5)
+    assert list(got["mismatch"]) == [0, 0, 0]
+    assert list(got["first_mismatch"]) == [-1, -1, -1]
+    assert got["no_majority"] == 0 and got["first_no_majority"] == -1
+
+
+def test_cfg1_full():
+    p = synth.cfg1()
+    assert_same(gpu_vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol),
+                oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
+
+
+def test_cfg2_scaled_ragged():
+    p = synth.cfg2(n=(1 << 22) + 37, flip_rate=1e-4)
+    assert_same(gpu_vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol),
+                oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
+
+
+def test_cfg3_scaled_ties():
+    for p in synth.cfg3(n=(1 << 18) + 5, block=1 << 12, ties=256):
+        ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        assert ref["no_majority"] >= 256
+        assert_same(gpu_vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), ref, p.R)
+
+
+def test_nontransitive_and_paper_delta():
+    # A~B, B~C, A!~C under rel 2^-10; and the paper's 0.1% delta for f32
+    a = np.array([1024.0, 1024.0, 1026.0, 1.0, 1.0], dtype=np.float32)
+    b = np.array([1025.0, 1026.0, 1024.0, 1.0009, 1.002], dtype=np.float32)
+    c = np.array([1026.0, 1025.0, 1025.0, 0.9995, 1.0], dtype=np.float32)
+    for rel in (2.0 ** -10, 1e-3):
+        assert_same(gpu_vote([a, b, c], "f32", 0.0, rel), oracle.vote([a, b, c], "f32", 0.0, rel), 3)
+
+
+def test_cfg2_full_size():
+    """The 256M-element f32 workload at full size, in the bench's launch
+    configuration, against the whole oracle run."""
+    p = synth.cfg2()
+    ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+    got = gpu_vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+    assert_same(got, ref, p.R)
+    # the flips that are real faults are all found in replica 2
+    assert got["mismatch"][2] > 0 and got["mismatch"][0] == 0
+
+
+def test_cfg3_full_size():
+    for p in synth.cfg3():
+        ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        got = gpu_vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        assert_same(got, ref, p.R)
+        assert got["mismatch"][3] >= (1 << 20) - 1024
