@@ -253,6 +253,9 @@ def run_ours(args, problem, ws, rank, local):
         del host
 
     s = fv.parse_stats(stats, R)
+    del reps, out, crc
+    batched = run_batched(args, dev, stream) if args.batched_tasks > 0 else None
+    serving = run_serving(args, dev) if args.serve_seconds > 0 else None
     if rank != 0:
         return
     cpu = None
@@ -280,8 +283,121 @@ def run_ours(args, problem, ws, rank, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "result": {"mismatch": s["mismatch"], "no_majority": s["no_majority"]},
+        "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
+
+
+def device_tasks(specs, dev, config_id, threads, stats_ptr=True):
+    """Generate each task's replicas with the seeded generator (a thread pool,
+    in bounded chunks) and upload them; returns the device buffers and a
+    ctypes array of descriptors."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    n = len(specs)
+    keep = []
+    descs = (fv.ft_vote_desc * n)()
+    stats = torch.empty((n, 18), dtype=torch.int64, device=dev)
+    nbytes_total = 0
+    chunk = max(threads * 4, 16)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for c0 in range(0, n, chunk):
+            probs = list(ex.map(lambda sp: synth.task_problem(sp, config_id=config_id), specs[c0:c0 + chunk]))
+            for k, p in enumerate(probs):
+                i = c0 + k
+                reps = [torch.from_numpy(r.view(np.uint8)).to(dev, non_blocking=False) for r in p.replicas]
+                nb = p.n * p.itemsize
+                out = torch.empty(max(nb, 16), dtype=torch.uint8, device=dev)
+                crc = torch.empty(max(1, fv.n_blocks(nb)), dtype=torch.int32, device=dev)
+                descs[i] = fv.make_desc(reps, out, crc, stats[i] if stats_ptr else None, p.abs_tol, p.rel_tol,
+                                        dtype=p.dtype, n=p.n)
+                keep.append((reps, out, crc))
+                nbytes_total += p.bytes_moved
+    return keep, descs, stats, nbytes_total
+
+
+def run_batched(args, dev, stream):
+    """4096 tasks (n log-uniform 1K..4M, f32/f64/i32 40/30/30 %, R=3, one
+    faulty replica in 5 % of the tasks): one graph-replayed batched vote
+    against 4096 plain ft_vote calls (ft_vote_many) on the same buffers."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    specs = synth.cfg4_specs(ntasks=args.batched_tasks)
+    t0 = time.perf_counter()
+    keep, descs, stats, nbytes = device_tasks(specs, dev, 4, host_cores())
+    gen_s = time.perf_counter() - t0
+    sh = int(stream.cuda_stream)
+    plan = ctypes.c_void_p()
+    t0 = time.perf_counter()
+    fv.check(fv.ft_plan_create(ctypes.byref(plan), descs, len(specs), None), "ft_plan_create")
+    plan_s = time.perf_counter() - t0
+    tune = fv.ft_tune()
+    fv.ft_plan_tune(plan, ctypes.byref(tune))
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    l0 = fv.ft_launch_count()
+    t_b = timed(lambda: fv.check(fv.ft_vote_batched(plan, sh), "batched"), args.batched_reps)
+    launches_b = (fv.ft_launch_count() - l0) // (args.batched_reps + 3)
+    t_p = timed(lambda: fv.check(fv.ft_vote_many(descs, len(specs), sh), "many"), max(2, args.batched_reps // 4))
+    fv.ft_plan_destroy(plan)
+    del keep, stats
+    torch.cuda.empty_cache()
+    return {"workload": f"{len(specs)} tasks, n log-uniform [2^10, 2^22], f32/f64/i32 40/30/30 %, R=3, "
+                        "one replica with bit flips (1e-4/element) in 5 % of tasks",
+            "tasks_per_s": round(len(specs) / t_b, 1), "gb_per_s": round(nbytes / t_b / 1e9, 1),
+            "ms_per_batch": round(t_b * 1e3, 3), "bytes_per_batch": nbytes,
+            "launches_per_batch": int(launches_b), "tune": {"tile_blocks": tune.tile_blocks,
+                                                            "ctas_per_sm": tune.ctas_per_sm},
+            "per_task_launches": {"tasks_per_s": round(len(specs) / t_p, 1), "gb_per_s": round(nbytes / t_p / 1e9, 1),
+                                  "ms_per_batch": round(t_p * 1e3, 3)},
+            "speedup_vs_per_task": round(t_p / t_b, 2),
+            "setup_s": {"generate_upload": round(gen_s, 1), "plan_create_autotune": round(plan_s, 2)}}
+
+
+def run_serving(args, dev):
+    """Poisson arrivals at 20k requests/s of votes with n log-uniform 4K..16M,
+    R in {3, 5}, f32/f64, under a 40 GB budget, replicas resident: continuous
+    batching against one-request batches (unbatched) on the same stream."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    from paper_1405_2912_b300 import serving
+    reqs, specs = synth.cfg5_requests(duration_s=args.serve_seconds, rate=args.serve_rate, pool=args.serve_pool)
+    keep, descs, _, _ = device_tasks(specs, dev, 5, host_cores(), stats_ptr=False)
+    torch.cuda.synchronize()
+    arrivals = np.array([r.t_arrival for r in reqs])
+    payload = np.array([r.payload for r in reqs])
+    per_req = np.array([(specs[r.payload].R + 1) * r.n * (4 if r.dtype == "f32" else 8) for r in reqs])
+    out = {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds} s, n log-uniform "
+                       "[2^12, 2^24], R in {3,5}, f32/f64 50/50, 40 GB budget, "
+                       f"{len(specs)} resident payloads",
+           "offered_gb_per_s": round(float(per_req.sum()) / args.serve_seconds / 1e9, 1)}
+    for name, slots, streams in (("continuous_batching", 4096, 3), ("unbatched", 1, 3)):
+        cfg = fv.ft_server_config(int(40e9), slots, streams, 8, 0)
+        srv = ctypes.c_void_p()
+        fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
+        try:
+            warm = min(len(reqs), 200)
+            serving.replay(srv, descs, arrivals[:warm] - arrivals[0], payload[:warm])
+            r = serving.replay(srv, descs, arrivals, payload)
+        finally:
+            fv.ft_server_destroy(srv)
+        out[name] = serving.summarize(r, per_req)
+    del keep
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -295,6 +411,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 28, help="elements the oracle votes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=1 << 26, help="elements per reference step")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
+    ap.add_argument("--batched-tasks", type=int, default=4096, help="tasks of the batched workload (0 = skip)")
+    ap.add_argument("--batched-reps", type=int, default=20)
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the request stream (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-pool", type=int, default=64)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.warmup < 3 and args.impl == "ours":
