@@ -154,6 +154,32 @@ int ft_plan_tune(const ft_plan *plan, ft_tune *out);
 
 int ft_plan_destroy(ft_plan *plan);
 
+/* ---- batched vote without any allocation ---- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: code running inside a framework whose pool
+ * owns all device memory, latency-critical loops where cudaMalloc / cudaFree
+ * would synchronise the device, plug-ins that must not change the process's
+ * allocation pattern.  It votes `ntasks` tasks (descriptors as for ft_vote,
+ * read during the call) like ft_vote_batched, but keeps its scratch (task
+ * table, per-task first tile, tile counters) in a fixed array of device
+ * memory inside the library (about 580 KiB, held on every GPU that loads the
+ * library until the process exits) and builds the batch in fixed host
+ * buffers: the call allocates nothing, neither with cudaMalloc nor on the
+ * host.  The caller still owns every input and output buffer.
+ *   ntasks       0 .. FT_NOALLOC_MAX_TASKS; more is rejected with FT_EINVAL.
+ *   tile_blocks  4 KiB blocks per work tile, 1 .. 64 (0 = 8).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (counters and
+ * statistics are reset at the start of each call): calls whose work overlaps
+ * on the GPU race on it, so order them on one stream or synchronise between
+ * them.  Host threads are serialised while a call builds its batch.
+ * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
+#define FT_NOALLOC_MAX_TASKS 4096
+int ft_vote_batched_noalloc(const ft_vote_desc *tasks, int32_t ntasks, int32_t tile_blocks,
+                            ft_stream stream);
+
 /* ---- serving form: continuous batching of vote requests ---- */
 
 typedef struct ft_server ft_server;   /* library-owned */

@@ -106,6 +106,9 @@ ft_server_destroy = _sig("ft_server_destroy", ctypes.c_int, _P)
 ft_server_pause = _sig("ft_server_pause", ctypes.c_int, _P, ctypes.c_int32)
 ft_clock_us = _sig("ft_clock_us", ctypes.c_double)
 ft_vote_many = _sig("ft_vote_many", ctypes.c_int, ctypes.POINTER(ft_vote_desc), ctypes.c_int32, _P)
+ft_vote_batched_noalloc = _sig("ft_vote_batched_noalloc", ctypes.c_int, ctypes.POINTER(ft_vote_desc),
+                               ctypes.c_int32, ctypes.c_int32, _P)
+FT_NOALLOC_MAX_TASKS = 4096
 ft_strerror = _sig("ft_strerror", ctypes.c_char_p, ctypes.c_int)
 ft_last_cuda_error = _sig("ft_last_cuda_error", ctypes.c_int)
 ft_launch_count = _sig("ft_launch_count", ctypes.c_uint64)
