@@ -151,6 +151,12 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def config_of(problem, ws):
+    return {"workload": WORKLOAD, "R": problem.R, "n": problem.n, "bytes_per_step": problem.bytes_moved,
+            "l2": "inputs (4 GiB per step) exceed the 126 MB L2; no flush",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
+
 def run_reference(args, problem):
     cores = host_cores()
     n_sample = min(problem.n, args.ref_sample)
@@ -168,7 +174,7 @@ def run_reference(args, problem):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "R": problem.R, "n": problem.n},
+            "config": config_of(problem, 1),
             "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -270,9 +276,7 @@ def run_ours(args, problem, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "R": R, "n": n, "bytes_per_step": bytes_step,
-                   "l2": "inputs (4 GiB per step) exceed the 126 MB L2; no flush",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "config": config_of(problem, ws),
         "hbm_frac_of_8tbs_spec": round(value / ws / 8000.0, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,

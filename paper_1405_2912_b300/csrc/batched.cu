@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
         const unsigned long long b0 = k * (unsigned long long)g.tile_blocks;
         const unsigned long long b1 = min(b0 + (unsigned long long)g.tile_blocks, a.nfull);
         for (unsigned long long b = b0; b < b1; ++b)
-            vote_full_block<K, R>(a, b, b + 1 < b1 ? b + 1 : ~0ull, tile, s_crc, s_comb, L, st, lane);
+            vote_full_block<K, R>(a, b, (VotePolicy<K, R>::kPrefetch && b + 1 < b1) ? b + 1 : ~0ull, tile, s_crc,
+                                  s_comb, L, st, lane);
         if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
@@ -71,12 +72,36 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
     if (cur >= 0) st.flush(cur_stats, lane);
 }
 
-constexpr int kBatchWarps = 16;
-
 template <int K, int R>
 static const void *group_fn()
 {
-    return reinterpret_cast<const void *>(batched_kernel<K, R, kBatchWarps>);
+    return reinterpret_cast<const void *>(batched_kernel<K, R, VotePolicy<K, R>::kWarps>);
+}
+
+template <int K>
+static int group_warps_k(int R)
+{
+    switch (R) {
+    case 2: return VotePolicy<K, 2>::kWarps;
+    case 3: return VotePolicy<K, 3>::kWarps;
+    case 4: return VotePolicy<K, 4>::kWarps;
+    case 5: return VotePolicy<K, 5>::kWarps;
+    case 6: return VotePolicy<K, 6>::kWarps;
+    case 7: return VotePolicy<K, 7>::kWarps;
+    default: return VotePolicy<K, 8>::kWarps;
+    }
+}
+
+// Warps per CTA of the batched kernel for (kind, R).
+static int group_warps(int kind, int R)
+{
+    switch (kind) {
+    case K_F32: return group_warps_k<K_F32>(R);
+    case K_F64: return group_warps_k<K_F64>(R);
+    case K_B1: return group_warps_k<K_B1>(R);
+    case K_B4: return group_warps_k<K_B4>(R);
+    default: return group_warps_k<K_B8>(R);
+    }
 }
 
 template <int K>
@@ -110,7 +135,8 @@ int group_occupancy(int kind, int R, int *sms, int *per_sm)
 {
     const void *fn = group_kernel(kind, R);
     if (!fn) return FT_EINVAL;
-    return occupancy(fn, kBatchWarps * 32, Smem::bytes(kBatchWarps), sms, per_sm);
+    const int warps = group_warps(kind, R);
+    return occupancy(fn, warps * 32, Smem::bytes(warps), sms, per_sm);
 }
 
 int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
@@ -118,17 +144,18 @@ int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
     const void *fn = group_kernel(g.kind, g.R);
     if (!fn) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
-    const size_t smem = Smem::bytes(kBatchWarps);
+    const int warps = group_warps(g.kind, g.R);
+    const size_t smem = Smem::bytes(warps);
     int sms = 0, per_sm = 0;
-    int rc = occupancy(fn, kBatchWarps * 32, smem, &sms, &per_sm);
+    int rc = occupancy(fn, warps * 32, smem, &sms, &per_sm);
     if (rc != FT_OK) return rc;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     unsigned long long grid = (unsigned long long)sms * per_sm;
-    const unsigned long long need = (g.total_tiles + kBatchWarps - 1) / kBatchWarps;
+    const unsigned long long need = (g.total_tiles + warps - 1) / warps;
     if (grid > need) grid = need;
     GroupDev arg = g;
     void *params[] = {&arg};
-    const cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kBatchWarps * 32), params, smem, s);
+    const cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(warps * 32), params, smem, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return check_launch(1);
 }

@@ -381,26 +381,31 @@ __device__ __forceinline__ void vote_elem(const typename Elem<K>::V (&x)[R], typ
     m = (~Ew & ((1u << R) - 1u)) | ((2 * best > R) ? 0u : (1u << R));
 }
 
+// Exact vote of one element, not inlined: the rare path of the kinds whose
+// fast path compares bits first.
+template <int K, int R>
+__device__ __noinline__ void vote_elem_call(typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
+                                            typename Elem<K>::V &y, uint32_t &m)
+{
+    vote_elem<K, R>(x, c, y, m);
+}
+
 // Fast form: the winner's bits, and `flag` raised whenever the element may
 // have a mismatch or no majority (a superset; the exact statistics are then
 // recomputed with vote_elem).
+//   f32:         R = 3 closed form, other R the exact form, both branch-free
+//                (ULP-level disagreements are common in float results);
+//   integers:    R = 3 closed form; other R: equal bits in all replicas give
+//                replica 0 at once, anything else takes the exact form;
+//   f64:         equal bits first for every R (FP64 arithmetic is slow).
 template <int K, int R>
 __device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
                                           typename Elem<K>::V &y, bool &flag)
 {
     using E = Elem<K>;
-    if constexpr (E::kBitsFirst) {
-        bool same = true;
-#pragma unroll
-        for (int r = 1; r < R; ++r) same &= (x[r] == x[0]);
-        if (same) {
-            y = x[0];
-        } else {
-            uint32_t m;
-            vote_elem<K, R>(x, c, y, m);
-            flag |= (m != 0);
-        }
-    } else if constexpr (R == 3) {
+    constexpr bool kClosed3 = (R == 3) && !E::kBitsFirst;
+    constexpr bool kBitsPath = E::kBitsFirst || (K != K_F32 && !kClosed3);
+    if constexpr (kClosed3) {
         // supports (1+e01+e02, 1+e01+e12, 1+e02+e12): replica 1 wins iff
         // e12 and not e02; replica 2 iff e02, e12 and not e01; else replica 0.
         // A mismatch or a missing majority needs not (e01 and e02), except in
@@ -411,6 +416,20 @@ __device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typ
         const bool w2 = e02 & e12 & !e01;
         y = w2 ? x[2] : (w1 ? x[1] : x[0]);
         flag |= !(e01 & e02);
+    } else if constexpr (kBitsPath) {
+        bool same = true;
+#pragma unroll
+        for (int r = 1; r < R; ++r) same &= (x[r] == x[0]);
+        if (same) {
+            y = x[0];
+        } else {
+            typename E::V xc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) xc[r] = x[r];
+            uint32_t m;
+            vote_elem_call<K, R>(xc, c, y, m);
+            flag |= (m != 0);
+        }
     } else {
         uint32_t m;
         vote_elem<K, R>(x, c, y, m);
@@ -509,6 +528,25 @@ __device__ __forceinline__ void store_elem(uint8_t *p, typename Elem<K>::V v)
     else *p = (uint8_t)v;
 }
 
+// 16-byte vectors per lane that a sub-batch loads from each replica.  (4 for
+// R = 5..6 of the kinds with the equal-bits fast path measured the same as 2
+// on the 5 x 64M f64 / i32 workloads and spilled.)
+template <int K, int R>
+constexpr int kSubBatch = (R <= 2) ? 8 : (R <= 4 ? 4 : 2);
+
+// Launch shape of the voter kernels for one (kind, R), chosen by measurement
+// on B300 (3 x 256M f32; 5 x 64M f64 and i32): warps per CTA (one CTA per SM)
+// and whether a warp prefetches its next block into L2 while voting the
+// current one.  The f32 R <= 3 vote is ALU-heavier per byte and gains from the
+// prefetch with 12 warps (6.7 TB/s against 6.2 with 16); the kinds with the
+// equal-bits fast path run best with 16 warps and no prefetch, whose extra L2
+// footprint costs more than it hides there.
+template <int K, int R>
+struct VotePolicy {
+    static constexpr bool kPrefetch = (K == K_F32 && R <= 3);
+    static constexpr int kWarps = kPrefetch ? 12 : 16;
+};
+
 // Exact statistics of the elements of lane `lane`'s vectors j0 .. j0+JB-1 of
 // block b, recomputed from global memory (rare path).
 template <int K, int R, int JB>
@@ -554,7 +592,7 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     using E = Elem<K>;
     using V = typename E::V;
     constexpr int kPerVec = 16 / E::kSize;
-    constexpr int JB = (R <= 2) ? 8 : (R <= 4 ? 4 : 2);      // vectors per lane per sub-batch
+    constexpr int JB = kSubBatch<K, R>;                      // vectors per lane per sub-batch
     const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
     const unsigned long long boff = b * kBlockBytes;
     if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);

@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
     const unsigned long long step = (unsigned long long)gridDim.x * W;
     const unsigned long long gw = (unsigned long long)blockIdx.x * W + w;
     for (unsigned long long b = gw; b < a.nfull; b += step)
-        vote_full_block<K, R>(a, b, b + step, tile, s_crc, s_comb, L, st, lane);
+        vote_full_block<K, R>(a, b, VotePolicy<K, R>::kPrefetch ? b + step : ~0ull, tile, s_crc, s_comb, L, st,
+                              lane);
     if (a.tail_bytes && a.nfull % step == gw) {
         // the partial last block goes to the warp whose turn it would be
         LaneStats<R> ts;
@@ -168,11 +169,10 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
     st.flush(a.stats, lane);
 }
 
-constexpr int kVoteWarps = 16;
-
 template <int K, int R>
 static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
 {
+    constexpr int kVoteWarps = VotePolicy<K, R>::kWarps;
     auto fn = vote_kernel<K, R, kVoteWarps>;
     const size_t smem = Smem::bytes(kVoteWarps);
     int sms = 0, per_sm = 0;
@@ -246,6 +246,11 @@ __global__ void __launch_bounds__(W * 32, 1)
     CrcLane L;
     L.init(lane);
     const unsigned long long step = (unsigned long long)gridDim.x * W;
+    // The warp's full 4 KiB chunks form one sequence across its blocks; the
+    // next chunk of the sequence is loaded into registers while the current
+    // one is digested.
+    uint4 q[8];
+    bool have = false;   // q holds chunk 0 of block b
     for (unsigned long long b = (unsigned long long)blockIdx.x * W + w; b < nblocks; b += step) {
         const unsigned long long start = b * block_bytes;
         const unsigned long long len = min((unsigned long long)block_bytes, nbytes - start);
@@ -256,14 +261,27 @@ __global__ void __launch_bounds__(W * 32, 1)
             const unsigned long long nl = min((unsigned long long)block_bytes, nbytes - ns) & ~15ull;
             for (unsigned long long o = 0; o < nl; o += 65536) prefetch_l2(buf + ns + o, (uint32_t)min(65536ull, nl - o));
         }
-        uint32_t acc = 0;
-        for (unsigned long long c = 0; c < nfull; ++c) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(buf + start + c * kBlockBytes);
-            uint4 q[8];
+        if (nfull && !have) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(buf + start);
 #pragma unroll
             for (int t = 0; t < 8; ++t) q[t] = __ldcs(src + lane + 32 * t);
+        }
+        have = false;
+        uint32_t acc = 0;
+        for (unsigned long long c = 0; c < nfull; ++c) {
 #pragma unroll
             for (int t = 0; t < 8; ++t) tile[tile_index(lane + 32 * t)] = q[t];
+            const uint4 *next = nullptr;
+            if (c + 1 < nfull) {
+                next = reinterpret_cast<const uint4 *>(buf + start + (c + 1) * kBlockBytes);
+            } else if (b + step < nblocks && nbytes - (b + step) * block_bytes >= (unsigned long long)kBlockBytes) {
+                next = reinterpret_cast<const uint4 *>(buf + (b + step) * block_bytes);
+                have = true;
+            }
+            if (next) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) q[t] = __ldcs(next + lane + 32 * t);
+            }
             __syncwarp();
             acc = shift_4096(acc) ^ tile_crc_full(tile, s_crc, s_comb, L, lane);
             __syncwarp();
