@@ -39,6 +39,38 @@ WORKLOAD = ("3 x 256M float32 replicas (lognormal sigma 2, random sign; +-1..4 U
 FALLBACK_HBM_GBS = 6400.0
 
 
+KERNEL_SOURCES = ("paper_1405_2912_b300/csrc/common.cuh", "paper_1405_2912_b300/csrc/vote.cu")
+TRAFFIC_FILE = "profiles/vote_f32_r3_256M_dram.txt"
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes (read + write) of one voter launch on this workload, from the
+    ncu capture recorded in TRAFFIC_FILE, if the kernel sources are still the
+    ones it was taken on; else None."""
+    path = os.path.join(ROOT, TRAFFIC_FILE)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if "=" in line:
+                k, v = (x.strip() for x in line.split("=", 1))
+                kv[k] = v
+    if kv.get("kernel_sources_sha256") != kernel_sources_hash():
+        return None
+    return float(kv["dram_bytes_read_per_launch"]) + float(kv["dram_bytes_write_per_launch"])
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -280,7 +312,8 @@ def run_ours(args, problem, ws, rank, local):
         "hbm_frac_of_8tbs_spec": round(value / ws / 8000.0, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "traffic": args.traffic,
+                     "traffic": args.traffic if args.traffic is not None else (
+                         measured_traffic() if n == 1 << 28 else None),
                      "kernel": "vote_kernel<F32,R=3> + stats reset (one ft_vote)"},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -236,6 +236,42 @@ int ft_server_destroy(ft_server *srv);
 /* The monotonic host clock (microseconds) of ft_result.submit_us / done_us. */
 double ft_clock_us(void);
 
+/* ---- fault-aware rating of processing units (Sec. IV.B) ---- */
+
+/* One kernel x processing-unit combination: its fault-free runtime (any time
+ * unit) and how many of its runs were valid.  Host memory, caller-owned. */
+typedef struct ft_unit_rating {
+    double   runtime;
+    uint64_t valid_runs;
+    uint64_t total_runs;
+} ft_unit_rating;
+
+/* Observed fault probability p = (total - valid) / total (0 with no runs; the
+ * paper prints v/t, read here as the share of faulty runs, which its own
+ * example p = 0.75 -> four times the runtime requires). */
+double ft_fault_probability(uint64_t valid_runs, uint64_t total_runs);
+
+/* Fault-aware runtime F = runtime / (1 - p) (Sec. IV.B): the runtime stretched
+ * by the expected number of attempts until a run is correct; +INFINITY when
+ * every run so far was faulty (p = 1); NaN if valid_runs > total_runs. */
+double ft_fault_aware_runtime(double runtime, uint64_t valid_runs, uint64_t total_runs);
+
+/* Fold one vote into the ratings: replica r was produced by unit
+ * unit_of_replica[r]; that run counts as valid iff stats->mismatch[r] == 0.
+ * stats is a HOST copy of the vote's ft_stats.  Returns FT_OK or FT_EINVAL. */
+int ft_rating_record(ft_unit_rating *units, int32_t nunits, const int32_t *unit_of_replica,
+                     int32_t R, const ft_stats *stats);
+
+/* Units in order of increasing F (ties keep index order) into order[0..count).
+ * Units whose F is infinite are left out except in check rounds (round a
+ * multiple of check_interval > 0), where they come first so that they run:
+ * the paper uses a unit that always failed only at predefined check intervals,
+ * to see whether it is still malfunctioning (Sec. IV.B).
+ * The first entry is the light-weight mode's choice (Sec. IV.C), the first two
+ * the DMR pair (Sec. IV.D).  Returns FT_OK or FT_EINVAL. */
+int ft_rating_rank(const ft_unit_rating *units, int32_t nunits, uint64_t round,
+                   uint64_t check_interval, int32_t *order, int32_t *count);
+
 /* ---- misc ---- */
 const char *ft_strerror(int code);
 int         ft_last_cuda_error(void);     /* cudaError_t of the last FT_ECUDA in this thread */

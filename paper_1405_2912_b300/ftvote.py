@@ -76,6 +76,10 @@ class ft_result(ctypes.Structure):
                 ("done_us", ctypes.c_double)]
 
 
+class ft_unit_rating(ctypes.Structure):
+    _fields_ = [("runtime", ctypes.c_double), ("valid_runs", ctypes.c_uint64), ("total_runs", ctypes.c_uint64)]
+
+
 assert ctypes.sizeof(ft_stats) == 144
 assert ctypes.sizeof(ft_vote_desc) == 8 * FT_MAX_R + 8 + 8 + 16 + 24
 
@@ -109,6 +113,14 @@ ft_vote_many = _sig("ft_vote_many", ctypes.c_int, ctypes.POINTER(ft_vote_desc), 
 ft_vote_batched_noalloc = _sig("ft_vote_batched_noalloc", ctypes.c_int, ctypes.POINTER(ft_vote_desc),
                                ctypes.c_int32, ctypes.c_int32, _P)
 FT_NOALLOC_MAX_TASKS = 4096
+ft_fault_probability = _sig("ft_fault_probability", ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64)
+ft_fault_aware_runtime = _sig("ft_fault_aware_runtime", ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                              ctypes.c_uint64)
+ft_rating_record = _sig("ft_rating_record", ctypes.c_int, ctypes.POINTER(ft_unit_rating), ctypes.c_int32,
+                        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ft_stats))
+ft_rating_rank = _sig("ft_rating_rank", ctypes.c_int, ctypes.POINTER(ft_unit_rating), ctypes.c_int32,
+                      ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                      ctypes.POINTER(ctypes.c_int32))
 ft_strerror = _sig("ft_strerror", ctypes.c_char_p, ctypes.c_int)
 ft_last_cuda_error = _sig("ft_last_cuda_error", ctypes.c_int)
 ft_launch_count = _sig("ft_launch_count", ctypes.c_uint64)
