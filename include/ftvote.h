@@ -236,6 +236,34 @@ int ft_server_destroy(ft_server *srv);
 /* The monotonic host clock (microseconds) of ft_result.submit_us / done_us. */
 double ft_clock_us(void);
 
+/* ---- digest-driven checkpoint of a device buffer (Sec. IV.A, IV.C) ---- */
+
+/* The paper's memory manager transfers data only when necessary and keeps a
+ * backup copy so that a faulty run can be rolled back.  A checkpoint context
+ * keeps the per-4-KiB CRC32C digests of the last checkpoint of one device
+ * buffer of nbytes bytes and moves only the blocks whose digest changed.  A
+ * change that leaves a block's CRC32C unchanged is not seen (a random change
+ * escapes with probability 2^-32; changes of a few bits never do).
+ * The context owns device memory for the digests and a block list and a
+ * staging area of stage_bytes (0 = 64 MiB), plus as much pinned host memory. */
+typedef struct ft_ckpt ft_ckpt;   /* library-owned */
+int ft_ckpt_create(ft_ckpt **ckpt, uint64_t nbytes, uint64_t stage_bytes);
+
+/* Bring host_copy (host memory, nbytes) up to date with dev_buf (device,
+ * 16-byte aligned): the first call copies every block, later calls only the
+ * blocks whose digest changed since the previous sync.  Synchronous (returns
+ * when host_copy is updated).  *blocks_copied (may be NULL) = blocks moved. */
+int ft_ckpt_sync(ft_ckpt *ckpt, const void *dev_buf, void *host_copy, ft_stream stream,
+                 uint64_t *blocks_copied);
+
+/* Roll dev_buf back to the checkpoint held in host_copy: uploads only the
+ * blocks whose current device digest differs from the checkpoint's (all
+ * blocks if no sync happened yet).  Synchronous. */
+int ft_ckpt_restore(ft_ckpt *ckpt, void *dev_buf, const void *host_copy, ft_stream stream,
+                    uint64_t *blocks_copied);
+
+int ft_ckpt_destroy(ft_ckpt *ckpt);
+
 /* ---- fault-aware rating of processing units (Sec. IV.B) ---- */
 
 /* One kernel x processing-unit combination: its fault-free runtime (any time

@@ -121,6 +121,10 @@ ft_rating_record = _sig("ft_rating_record", ctypes.c_int, ctypes.POINTER(ft_unit
 ft_rating_rank = _sig("ft_rating_rank", ctypes.c_int, ctypes.POINTER(ft_unit_rating), ctypes.c_int32,
                       ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
                       ctypes.POINTER(ctypes.c_int32))
+ft_ckpt_create = _sig("ft_ckpt_create", ctypes.c_int, ctypes.POINTER(_P), ctypes.c_uint64, ctypes.c_uint64)
+ft_ckpt_sync = _sig("ft_ckpt_sync", ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64))
+ft_ckpt_restore = _sig("ft_ckpt_restore", ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64))
+ft_ckpt_destroy = _sig("ft_ckpt_destroy", ctypes.c_int, _P)
 ft_strerror = _sig("ft_strerror", ctypes.c_char_p, ctypes.c_int)
 ft_last_cuda_error = _sig("ft_last_cuda_error", ctypes.c_int)
 ft_launch_count = _sig("ft_launch_count", ctypes.c_uint64)

@@ -99,3 +99,12 @@ def test_clock_is_monotonic(fv):
     time.sleep(0.01)
     b = fv.ft_clock_us()
     assert b - a >= 9000
+
+
+def test_ckpt_argument_checks(fv):
+    c = ctypes.c_void_p()
+    assert fv.ft_ckpt_create(ctypes.byref(c), 0, 0) == fv.FT_EINVAL
+    assert fv.ft_ckpt_create(None, 100, 0) == fv.FT_EINVAL
+    assert fv.ft_ckpt_sync(None, 0x1000, 0x2000, None, None) == fv.FT_EINVAL
+    assert fv.ft_ckpt_restore(None, 0x1000, 0x2000, None, None) == fv.FT_EINVAL
+    assert fv.ft_ckpt_destroy(None) == fv.FT_EINVAL
