@@ -236,6 +236,42 @@ int ft_server_destroy(ft_server *srv);
 /* The monotonic host clock (microseconds) of ft_result.submit_us / done_us. */
 double ft_clock_us(void);
 
+/* ---- value types of buffers, and task duplication (Sec. IV.D, IV.E) ---- */
+
+/* The delta the paper chose for single precision after observing CPU/GPU
+ * results differ by 0.001 % to 0.1 % (Sec. IV.D), as a relative tolerance. */
+#define FT_PAPER_F32_REL_TOL 1e-3
+
+/* Register a device area (bytes, a multiple of the element size) with its
+ * value type and compare tolerances, as the paper's dls_register_data(ptr,
+ * size, type, mode) tells its runtime how to compare a buffer (Sec. IV.E).
+ * Areas may not overlap.  Returns FT_OK or FT_EINVAL. */
+int ft_register_data(const void *ptr, uint64_t bytes, int32_t dtype, double abs_tol, double rel_tol);
+int ft_unregister_data(const void *ptr);   /* FT_OK or FT_ENOTFOUND */
+
+/* Type, tolerances and bytes from ptr to the end of the registered area that
+ * contains ptr (any output pointer may be NULL).  FT_OK or FT_ENOTFOUND. */
+int ft_registered_type(const void *ptr, int32_t *dtype, double *abs_tol, double *rel_tol,
+                       uint64_t *bytes);
+
+/* ft_vote into `out`, a registered area: element type, tolerances and n come
+ * from its registration (n = bytes from out to the area's end / element size).
+ * replicas: host array of R device pointers.  FT_ENOTFOUND if out is not in a
+ * registered area. */
+int ft_vote_registered(const void *const *replicas, int32_t R, void *out, uint32_t *block_crc,
+                       ft_stats *stats, ft_stream stream);
+
+/* A duplicated task: computes replica `replica` of the task's result into
+ * `out` (device memory), on the GPU on `stream` or on the CPU followed by a
+ * copy; returns FT_OK or any nonzero code to abort. */
+typedef int (*ft_task_fn)(void *user, int32_t replica, void *out, ft_stream stream);
+
+/* Task duplication followed by the vote (Sec. IV.D): calls task(user, r,
+ * vote->replicas[r], stream) for r = 0..R-1, then ft_vote(vote, stream).  The
+ * task may use a different kernel or processing unit for each replica (the
+ * paper's HetDMR mode).  Returns the first nonzero task code, or ft_vote's. */
+int ft_dmr_run(ft_task_fn task, void *user, const ft_vote_desc *vote, ft_stream stream);
+
 /* ---- digest-driven checkpoint of a device buffer (Sec. IV.A, IV.C) ---- */
 
 /* The paper's memory manager transfers data only when necessary and keeps a

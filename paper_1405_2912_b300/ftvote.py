@@ -125,6 +125,16 @@ ft_ckpt_create = _sig("ft_ckpt_create", ctypes.c_int, ctypes.POINTER(_P), ctypes
 ft_ckpt_sync = _sig("ft_ckpt_sync", ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64))
 ft_ckpt_restore = _sig("ft_ckpt_restore", ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64))
 ft_ckpt_destroy = _sig("ft_ckpt_destroy", ctypes.c_int, _P)
+FT_PAPER_F32_REL_TOL = 1e-3
+ft_register_data = _sig("ft_register_data", ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                        ctypes.c_double)
+ft_unregister_data = _sig("ft_unregister_data", ctypes.c_int, _P)
+ft_registered_type = _sig("ft_registered_type", ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_uint64))
+ft_vote_registered = _sig("ft_vote_registered", ctypes.c_int, ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, _P)
+ft_task_fn = ctypes.CFUNCTYPE(ctypes.c_int, _P, ctypes.c_int32, _P, _P)
+ft_dmr_run = _sig("ft_dmr_run", ctypes.c_int, ft_task_fn, _P, ctypes.POINTER(ft_vote_desc), _P)
 ft_strerror = _sig("ft_strerror", ctypes.c_char_p, ctypes.c_int)
 ft_last_cuda_error = _sig("ft_last_cuda_error", ctypes.c_int)
 ft_launch_count = _sig("ft_launch_count", ctypes.c_uint64)
