@@ -231,6 +231,16 @@ __device__ __forceinline__ uint32_t shift_4096(uint32_t c)
 
 __device__ __forceinline__ int tile_index(int v) { return v + (v >> 3); }
 
+// Streaming 16-byte load of read-only data that bypasses L1 allocation.
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 {
@@ -604,7 +614,7 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
         for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj)
-                v[r][jj] = __ldcs(reinterpret_cast<const uint4 *>(a.rep[r] + boff) + lane + 32 * (j0 + jj));
+                v[r][jj] = ld_stream(reinterpret_cast<const uint4 *>(a.rep[r] + boff) + lane + 32 * (j0 + jj));
         bool flag = false;
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
@@ -628,6 +638,64 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);
     if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
     __syncwarp();
+}
+
+// Pipelined form of vote_full_block for small R: v holds all 8 vectors of
+// block b of every replica on entry.  The block is voted and stored, then the
+// loads of block b_next (if any) are issued into v before the block's CRC32C
+// runs, so that a warp has a whole block of loads in flight during its
+// digest instead of none.
+template <int K, int R>
+__device__ __forceinline__ void vote_full_block_pipelined(const TaskArgs &a, unsigned long long b,
+                                                          unsigned long long b_next, uint4 (&v)[R][8], uint4 *tile,
+                                                          const uint32_t *s_crc, const uint32_t *s_comb,
+                                                          const CrcLane &L, LaneStats<R> &st, int lane)
+{
+    using E = Elem<K>;
+    using V = typename E::V;
+    constexpr int kPerVec = 16 / E::kSize;
+    const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
+    const unsigned long long boff = b * kBlockBytes;
+    bool flag = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint4 yv = v[0][j];
+#pragma unroll
+        for (int e = 0; e < kPerVec; ++e) {
+            V x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = E::get(v[r][j], e);
+            V y;
+            vote_fast<K, R>(x, ctx, y, flag);
+            E::set(yv, e, y);
+        }
+        const int vi = lane + 32 * j;
+        __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
+        tile[tile_index(vi)] = yv;
+    }
+    if (b_next < a.nfull) {
+        const unsigned long long noff = b_next * kBlockBytes;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                v[r][j] = __ldcs(reinterpret_cast<const uint4 *>(a.rep[r] + noff) + lane + 32 * j);
+    }
+    if (flag) exact_stats<K, R, 8>(a, b, 0, lane, st);
+    __syncwarp();
+    const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);
+    if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
+    __syncwarp();
+}
+
+template <int R>
+__device__ __forceinline__ void load_block(const TaskArgs &a, unsigned long long b, uint4 (&v)[R][8], int lane)
+{
+    const unsigned long long off = b * kBlockBytes;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[r][j] = __ldcs(reinterpret_cast<const uint4 *>(a.rep[r] + off) + lane + 32 * j);
 }
 
 // The partial last block (a.tail_bytes bytes), element by element.
