@@ -640,64 +640,6 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     __syncwarp();
 }
 
-// Pipelined form of vote_full_block for small R: v holds all 8 vectors of
-// block b of every replica on entry.  The block is voted and stored, then the
-// loads of block b_next (if any) are issued into v before the block's CRC32C
-// runs, so that a warp has a whole block of loads in flight during its
-// digest instead of none.
-template <int K, int R>
-__device__ __forceinline__ void vote_full_block_pipelined(const TaskArgs &a, unsigned long long b,
-                                                          unsigned long long b_next, uint4 (&v)[R][8], uint4 *tile,
-                                                          const uint32_t *s_crc, const uint32_t *s_comb,
-                                                          const CrcLane &L, LaneStats<R> &st, int lane)
-{
-    using E = Elem<K>;
-    using V = typename E::V;
-    constexpr int kPerVec = 16 / E::kSize;
-    const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
-    const unsigned long long boff = b * kBlockBytes;
-    bool flag = false;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        uint4 yv = v[0][j];
-#pragma unroll
-        for (int e = 0; e < kPerVec; ++e) {
-            V x[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = E::get(v[r][j], e);
-            V y;
-            vote_fast<K, R>(x, ctx, y, flag);
-            E::set(yv, e, y);
-        }
-        const int vi = lane + 32 * j;
-        __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
-        tile[tile_index(vi)] = yv;
-    }
-    if (b_next < a.nfull) {
-        const unsigned long long noff = b_next * kBlockBytes;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                v[r][j] = __ldcs(reinterpret_cast<const uint4 *>(a.rep[r] + noff) + lane + 32 * j);
-    }
-    if (flag) exact_stats<K, R, 8>(a, b, 0, lane, st);
-    __syncwarp();
-    const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);
-    if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
-    __syncwarp();
-}
-
-template <int R>
-__device__ __forceinline__ void load_block(const TaskArgs &a, unsigned long long b, uint4 (&v)[R][8], int lane)
-{
-    const unsigned long long off = b * kBlockBytes;
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[r][j] = __ldcs(reinterpret_cast<const uint4 *>(a.rep[r] + off) + lane + 32 * j);
-}
-
 // The partial last block (a.tail_bytes bytes), element by element.
 template <int K, int R>
 __device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long long b, uint4 *tile,
