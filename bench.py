@@ -428,10 +428,18 @@ def run_serving(args, dev):
         try:
             warm = min(len(reqs), 200)
             serving.replay(srv, descs, arrivals[:warm] - arrivals[0], payload[:warm])
+            info0 = fv.ft_server_stats()
+            fv.ft_server_info(srv, ctypes.byref(info0))
             r = serving.replay(srv, descs, arrivals, payload)
+            info = fv.ft_server_stats()
+            fv.ft_server_info(srv, ctypes.byref(info))
         finally:
             fv.ft_server_destroy(srv)
         out[name] = serving.summarize(r, per_req)
+        nb = info.batches - info0.batches
+        out[name].update({"batches": int(nb),
+                          "mean_requests_per_batch": round((info.requests - info0.requests) / max(1, nb), 2),
+                          "max_batches_in_flight": int(info.max_batches_in_flight)})
     del keep
     torch.cuda.empty_cache()
     return out

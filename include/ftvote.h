@@ -233,6 +233,17 @@ int ft_server_pause(ft_server *srv, int32_t paused);
  * server during or after this call.  Returns FT_OK. */
 int ft_server_destroy(ft_server *srv);
 
+/* Counters of a server since its creation. */
+typedef struct ft_server_stats {
+    uint64_t batches;                /* batches launched                                 */
+    uint64_t requests;               /* requests launched in them                        */
+    uint64_t completed;              /* requests whose batch has completed               */
+    int32_t  max_batches_in_flight;  /* most batches on the device at the same time      */
+    int32_t  inflight_requests;      /* admitted, not yet collected                      */
+    uint64_t inflight_bytes;         /* their share of the budget                        */
+} ft_server_stats;
+int ft_server_info(ft_server *srv, ft_server_stats *out);
+
 /* The monotonic host clock (microseconds) of ft_result.submit_us / done_us. */
 double ft_clock_us(void);
 

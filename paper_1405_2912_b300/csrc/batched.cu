@@ -417,6 +417,42 @@ static int autotune(ft_plan *p, ft_tune *out)
     return FT_OK;
 }
 
+// Records the reset and the group kernels into the capture of stream s, the
+// group kernels as parallel branches after the reset (each on its own forked
+// stream), so that one group's CTAs can start on the SMs that the previous
+// group's CTAs leave at its tail.
+static int launch_batch_branches(ft_plan *p, cudaStream_t s)
+{
+    const BatchLayout &L = p->layout;
+    int rc = launch_batch_reset(L.tasks_dev, (int)L.tasks.size(), L.counters_dev, (int)p->gd.size(), s);
+    if (rc != FT_OK || p->gd.size() <= 1) {
+        for (const GroupDev &g : p->gd)
+            if (rc == FT_OK) rc = launch_group(g, p->tune.ctas_per_sm, s);
+        return rc;
+    }
+    const size_t k = p->gd.size();
+    std::vector<cudaStream_t> side(k, nullptr);
+    std::vector<cudaEvent_t> done(k, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+    for (size_t i = 0; i < k && e == cudaSuccess && rc == FT_OK; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(side[i], fork, 0)) != cudaSuccess) break;
+        rc = launch_group(p->gd[i], p->tune.ctas_per_sm, side[i]);
+        if (rc == FT_OK) e = cudaEventRecord(done[i], side[i]);
+    }
+    for (size_t i = 0; i < k && e == cudaSuccess && rc == FT_OK; ++i) e = cudaStreamWaitEvent(s, done[i], 0);
+    if (e != cudaSuccess && rc == FT_OK) rc = cuda_fail(e);
+    for (size_t i = 0; i < k; ++i) {
+        if (done[i]) cudaEventDestroy(done[i]);
+        if (side[i]) cudaStreamDestroy(side[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    return rc;
+}
+
 static int capture(ft_plan *p)
 {
     cudaStream_t s;
@@ -426,7 +462,7 @@ static int capture(ft_plan *p)
     const unsigned long long before = g_launches.load();
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) rc = cuda_fail(e);
     if (rc == FT_OK) {
-        rc = launch_batch(p->layout, p->gd, p->tune.ctas_per_sm, s);
+        rc = launch_batch_branches(p, s);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(s, &g);
         if (rc == FT_OK && e != cudaSuccess) rc = cuda_fail(e);

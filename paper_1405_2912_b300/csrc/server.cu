@@ -87,6 +87,9 @@ struct ft_server {
     bool paused = false;
     std::vector<Slot> slots;
     std::thread worker;
+    // counters reported by ft_server_info
+    unsigned long long batches = 0, batched_requests = 0, completed = 0;
+    int busy_now = 0, busy_max = 0;
 };
 
 namespace {
@@ -107,8 +110,10 @@ void CUDART_CB batch_done(void *p)
         r.done = true;
         r.done_us = t;
     }
+    s->completed += sl.tickets.size();
     sl.tickets.clear();
     sl.busy = false;
+    s->busy_now -= 1;
     s->cv_done.notify_all();
     s->cv_work.notify_all();
 }
@@ -205,6 +210,10 @@ void worker_main(ft_server *s)
         }
         if (args.empty()) continue;
         sl.busy = true;
+        s->batches += 1;
+        s->batched_requests += args.size();
+        s->busy_now += 1;
+        s->busy_max = std::max(s->busy_max, s->busy_now);
         std::vector<ft_stats *> users(args.size());
         for (size_t i = 0; i < args.size(); ++i) users[i] = s->reqs[sl.tickets[i]].user_stats;
         lk.unlock();
@@ -371,6 +380,19 @@ int ft_server_destroy(ft_server *s)
     }
     if (s->worker.joinable()) s->worker.join();
     free_server(s);
+    return FT_OK;
+}
+
+int ft_server_info(ft_server *s, ft_server_stats *out)
+{
+    if (!s || !out) return FT_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->batches = s->batches;
+    out->requests = s->batched_requests;
+    out->completed = s->completed;
+    out->max_batches_in_flight = s->busy_max;
+    out->inflight_requests = s->inflight;
+    out->inflight_bytes = s->inflight_bytes;
     return FT_OK;
 }
 

@@ -80,6 +80,12 @@ class ft_unit_rating(ctypes.Structure):
     _fields_ = [("runtime", ctypes.c_double), ("valid_runs", ctypes.c_uint64), ("total_runs", ctypes.c_uint64)]
 
 
+class ft_server_stats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("requests", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("max_batches_in_flight", ctypes.c_int32), ("inflight_requests", ctypes.c_int32),
+                ("inflight_bytes", ctypes.c_uint64)]
+
+
 assert ctypes.sizeof(ft_stats) == 144
 assert ctypes.sizeof(ft_vote_desc) == 8 * FT_MAX_R + 8 + 8 + 16 + 24
 
@@ -109,6 +115,7 @@ ft_poll = _sig("ft_poll", ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int64, cty
 ft_server_destroy = _sig("ft_server_destroy", ctypes.c_int, _P)
 ft_server_pause = _sig("ft_server_pause", ctypes.c_int, _P, ctypes.c_int32)
 ft_clock_us = _sig("ft_clock_us", ctypes.c_double)
+ft_server_info = _sig("ft_server_info", ctypes.c_int, _P, ctypes.POINTER(ft_server_stats))
 ft_vote_many = _sig("ft_vote_many", ctypes.c_int, ctypes.POINTER(ft_vote_desc), ctypes.c_int32, _P)
 ft_vote_batched_noalloc = _sig("ft_vote_batched_noalloc", ctypes.c_int, ctypes.POINTER(ft_vote_desc),
                                ctypes.c_int32, ctypes.c_int32, _P)

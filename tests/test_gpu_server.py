@@ -143,3 +143,31 @@ def test_bounded_wait_and_unknown_tickets():
         assert list(r.stats.mismatch)[:p.R] == [int(x) for x in ref["mismatch"]]
     finally:
         fv.ft_server_destroy(srv)
+
+
+def test_server_counters():
+    from paper_1405_2912_b300 import ftvote as fv
+    probs = _requests(k=12, seed=8)
+    tasks = [DevTask(p) for p in probs]
+    srv = _server(budget=1 << 34, max_slots=4, streams=2)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tks = []
+        for t in tasks:
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(t.desc), ctypes.byref(tk)) == fv.FT_OK
+            tks.append(tk.value)
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        assert info.batches == 0 and info.inflight_requests == 12
+        fv.ft_server_pause(srv, 0)
+        r = fv.ft_result()
+        for tk in tks:
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+        fv.ft_server_info(srv, ctypes.byref(info))
+        # 12 queued requests, at most 4 per batch: 3 batches, on up to 2 streams at once
+        assert info.batches == 3 and info.requests == 12 and info.completed == 12
+        assert 1 <= info.max_batches_in_flight <= 2
+        assert info.inflight_requests == 0 and info.inflight_bytes == 0
+    finally:
+        fv.ft_server_destroy(srv)
