@@ -110,9 +110,27 @@ constexpr int kCrcRowWords = 64;    // one 256-byte row per byte value: 4 tables
 constexpr int kCrcWords = 256 * kCrcRowWords;
 constexpr uint64_t kNone = ~0ull;   // "no index yet"; reads as -1 through int64
 
-// Shared-memory layout of a CTA: the slicing tables (row e holds T_k[e] for
-// k = 0..3, 16 copies each), the per-lane combine tables, then one padded
-// tile per warp.
+// The shared-memory image of the tables, built at compile time: the slicing
+// tables (row e holds T_k[e] for k = 0..3, 16 copies each) followed by the
+// per-lane combine tables.  A CTA copies it with 16-byte loads.
+struct alignas(16) CrcImage {
+    uint32_t w[kCrcWords + kCombWords];
+};
+
+constexpr CrcImage make_crc_image()
+{
+    CrcImage im{};
+    for (int i = 0; i < kCrcWords; ++i) im.w[i] = kCrcHost.slice[(i >> 4) & 3][i >> 6];
+    for (int p = 0; p < 8; ++p)
+        for (int v = 0; v < 16; ++v)
+            for (int l = 0; l < 32; ++l) im.w[kCrcWords + (p * 16 + v) * 32 + l] = kCrcHost.comb[p][v][l];
+    return im;
+}
+
+__device__ const CrcImage g_crc_image = make_crc_image();
+
+// Shared-memory layout of a CTA: the table image, then one padded tile per
+// warp.
 struct Smem {
     static __host__ __device__ constexpr size_t bytes(int warps)
     {
@@ -120,15 +138,14 @@ struct Smem {
     }
 };
 
+// s_comb must follow s_crc directly (kCrcWords words later).
 __device__ __forceinline__ void load_crc_tables(uint32_t *s_crc, uint32_t *s_comb)
 {
-    for (int i = threadIdx.x; i < kCrcWords; i += blockDim.x) {
-        const int e = i >> 6, k = (i >> 4) & 3;
-        s_crc[i] = g_crc.slice[k][e];
-    }
-    const uint4 *csrc = reinterpret_cast<const uint4 *>(&g_crc.comb[0][0][0]);
-    uint4 *cdst = reinterpret_cast<uint4 *>(s_comb);
-    for (int i = threadIdx.x; i < kCombWords / 4; i += blockDim.x) cdst[i] = csrc[i];
+    (void)s_comb;
+    const uint4 *src = reinterpret_cast<const uint4 *>(g_crc_image.w);
+    uint4 *dst = reinterpret_cast<uint4 *>(s_crc);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < (kCrcWords + kCombWords) / 4; i += blockDim.x) dst[i] = src[i];
 }
 
 // Per-lane constants of the table lookups.  Lane l reads copy l % 16.  In

@@ -7,9 +7,11 @@
 // waiting into the next batch (up to max_slots), lays the batch out for the
 // persistent batched kernels and launches it on one of `streams` CUDA
 // streams, so that a new batch starts while earlier ones are still on the
-// device.  A host callback enqueued after each batch marks its requests done;
-// ft_poll waits for that with a bound, as the paper's runtime bounds the wait
-// for a task by a timeout (Sec. IV.C).
+// device.  The worker detects completed batches by polling an event per batch
+// (spinning while batches are in flight, and for a short while after, before
+// it sleeps), marks their requests done, and ft_poll waits for that with a
+// bound, as the paper's runtime bounds the wait for a task by a timeout
+// (Sec. IV.C).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -44,15 +46,9 @@ struct Request {
     ft_stats result;
 };
 
-struct Slot;
-
-struct Callback {
-    ft_server *srv;
-    int slot;
-};
-
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;        // recorded after the batch's last copy
     uint8_t *dev = nullptr;            // batch layout (device)
     size_t dev_cap = 0;
     uint8_t *host = nullptr;           // batch layout staging (pinned)
@@ -67,7 +63,6 @@ struct Slot {
     std::vector<unsigned long long> tickets;
     ftv::BatchLayout layout;
     std::vector<ftv::GroupDev> gd;
-    Callback cb;
 };
 
 }  // namespace
@@ -94,13 +89,10 @@ struct ft_server {
 
 namespace {
 
-void CUDART_CB batch_done(void *p)
+// Mark the requests of slot si done (lock held).
+void complete_slot(ft_server *s, int si, double t)
 {
-    Callback *cb = static_cast<Callback *>(p);
-    ft_server *s = cb->srv;
-    const double t = now_us();
-    std::lock_guard<std::mutex> lk(s->mu);
-    Slot &sl = s->slots[cb->slot];
+    Slot &sl = s->slots[si];
     for (size_t i = 0; i < sl.tickets.size(); ++i) {
         auto it = s->reqs.find(sl.tickets[i]);
         if (it == s->reqs.end()) continue;
@@ -115,7 +107,6 @@ void CUDART_CB batch_done(void *p)
     sl.busy = false;
     s->busy_now -= 1;
     s->cv_done.notify_all();
-    s->cv_work.notify_all();
 }
 
 int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
@@ -179,22 +170,47 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     return FT_OK;
 }
 
+// Idle time the worker spins (yielding) before it sleeps on the condition
+// variable: a request that arrives within it is picked up without a wake-up.
+constexpr double kSpinUs = 200.0;
+
 void worker_main(ft_server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    double idle_since = now_us();
     for (;;) {
+        // 1. completions
+        bool any_busy = false;
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+            Slot &sl = s->slots[i];
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            if (q != cudaSuccess) sl.status = ftv::cuda_fail(q);
+            complete_slot(s, (int)i, now_us());
+        }
+        if (s->stop && !any_busy) break;
         int free_slot = -1;
         for (size_t i = 0; i < s->slots.size(); ++i)
             if (!s->slots[i].busy) { free_slot = (int)i; break; }
-        bool any_busy = false;
-        for (auto &sl : s->slots) any_busy |= sl.busy;
-        if (s->stop && !any_busy) break;
+        // 2. nothing to launch: spin while batches are in flight or shortly
+        //    after the last activity, else sleep until a request or stop
         if (s->stop || s->paused || s->pending.empty() || free_slot < 0) {
-            s->cv_work.wait(lk);
+            if (any_busy || now_us() - idle_since < kSpinUs) {
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                s->cv_work.wait(lk);
+                idle_since = now_us();
+            }
             continue;
         }
-        // take up to max_slots waiting requests (FIFO) into this slot
+        // 3. take up to max_slots waiting requests (FIFO) into this slot
         Slot &sl = s->slots[free_slot];
         std::vector<ftv::TaskArgs> args;
         sl.tickets.clear();
@@ -224,17 +240,17 @@ void worker_main(ft_server *s)
         }
         if (rc == FT_OK) rc = launch_slot(s, free_slot, args, any_user);
         sl.status = rc;
-        sl.cb = Callback{s, free_slot};
-        cudaError_t e = cudaLaunchHostFunc(sl.stream, batch_done, &sl.cb);
-        lk.lock();
+        cudaError_t e = cudaEventRecord(sl.done, sl.stream);
         if (e != cudaSuccess) {
-            // the completion callback could not be queued: finish the batch here
-            lk.unlock();
+            // no completion event: finish the batch here
             cudaStreamSynchronize(sl.stream);
             sl.status = ftv::cuda_fail(e);
-            batch_done(&sl.cb);
+            lk.lock();
+            complete_slot(s, free_slot, now_us());
+        } else {
             lk.lock();
         }
+        idle_since = now_us();
     }
 }
 
@@ -242,6 +258,7 @@ void free_server(ft_server *s)
 {
     for (auto &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
         if (sl.dev) cudaFree(sl.dev);
         if (sl.host) cudaFreeHost(sl.host);
         if (sl.dev_stats) cudaFree(sl.dev_stats);
@@ -280,7 +297,8 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     const unsigned long long tiles = cfg->mem_budget_bytes / (2ull * 4096ull * s->cfg.tile_blocks) + cfg->max_slots;
     const size_t guess = sizeof(ftv::TaskArgs) * cfg->max_slots + 8ull * cfg->max_slots + 4ull * tiles + 4096;
     for (auto &sl : s->slots) {
-        if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess) {
             rc = ftv::cuda_fail(e);
             break;
         }
