@@ -291,6 +291,23 @@ def run_ours(args, problem, ws, rank, local):
         del host
 
     s = fv.parse_stats(stats, R)
+    digest = None
+    if args.digest_reps > 0:
+        # ft_digest alone over the voted buffer (n * 4 bytes read per call)
+        dout = torch.empty_like(crc)
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fv.check(fv.ft_digest(out.data_ptr(), nbytes, 4096, dout.data_ptr(), sh), "ft_digest")
+            d0.record(stream)
+            for _ in range(args.digest_reps):
+                fv.ft_digest(out.data_ptr(), nbytes, 4096, dout.data_ptr(), sh)
+            d1.record(stream)
+        torch.cuda.synchronize()
+        t_d = d0.elapsed_time(d1) / 1e3 / args.digest_reps
+        digest = {"bytes_per_call": nbytes, "gb_per_s": round(nbytes / t_d / 1e9, 1),
+                  "us_per_call": round(t_d * 1e6, 1), "matches_fused_digest": bool(torch.equal(dout, crc))}
     del reps, out, crc
     batched = run_batched(args, dev, stream) if args.batched_tasks > 0 else None
     serving = run_serving(args, dev) if args.serve_seconds > 0 else None
@@ -320,6 +337,7 @@ def run_ours(args, problem, ws, rank, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "result": {"mismatch": s["mismatch"], "no_majority": s["no_majority"]},
+        "digest": digest,
         "batched": batched,
         "serving": serving,
     }
@@ -456,6 +474,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 28, help="elements the oracle votes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=1 << 26, help="elements per reference step")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
+    ap.add_argument("--digest-reps", type=int, default=50, help="timed ft_digest calls on the voted buffer (0 = skip)")
     ap.add_argument("--batched-tasks", type=int, default=4096, help="tasks of the batched workload (0 = skip)")
     ap.add_argument("--batched-reps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the request stream (0 = skip)")
