@@ -423,41 +423,46 @@ def run_batched(args, dev, stream):
 
 
 def run_serving(args, dev):
-    """Poisson arrivals at 20k requests/s of votes with n log-uniform 4K..16M,
-    R in {3, 5}, f32/f64, under a 40 GB budget, replicas resident: continuous
-    batching against one-request batches (unbatched) on the same stream."""
+    """Poisson arrivals of votes with n log-uniform 4K..16M, R in {3, 5},
+    f32/f64, under a 40 GB budget, replicas resident: continuous batching
+    (batches capped at 1 GB of request bytes) against one-request batches on
+    the same 3 streams, at the workload's 20k requests/s and at three times
+    that load."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     from paper_1405_2912_b300 import serving
-    reqs, specs = synth.cfg5_requests(duration_s=args.serve_seconds, rate=args.serve_rate, pool=args.serve_pool)
+    _, specs = synth.cfg5_requests(duration_s=args.serve_seconds, rate=args.serve_rate, pool=args.serve_pool)
     keep, descs, _, _ = device_tasks(specs, dev, 5, host_cores(), stats_ptr=False)
     torch.cuda.synchronize()
-    arrivals = np.array([r.t_arrival for r in reqs])
-    payload = np.array([r.payload for r in reqs])
-    per_req = np.array([(specs[r.payload].R + 1) * r.n * (4 if r.dtype == "f32" else 8) for r in reqs])
-    out = {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds} s, n log-uniform "
-                       "[2^12, 2^24], R in {3,5}, f32/f64 50/50, 40 GB budget, "
-                       f"{len(specs)} resident payloads",
-           "offered_gb_per_s": round(float(per_req.sum()) / args.serve_seconds / 1e9, 1)}
-    for name, slots, streams in (("continuous_batching", 4096, 3), ("unbatched", 1, 3)):
-        cfg = fv.ft_server_config(int(40e9), slots, streams, 8, 0)
-        srv = ctypes.c_void_p()
-        fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
-        try:
-            warm = min(len(reqs), 200)
-            serving.replay(srv, descs, arrivals[:warm] - arrivals[0], payload[:warm])
-            info0 = fv.ft_server_stats()
-            fv.ft_server_info(srv, ctypes.byref(info0))
-            r = serving.replay(srv, descs, arrivals, payload)
-            info = fv.ft_server_stats()
-            fv.ft_server_info(srv, ctypes.byref(info))
-        finally:
-            fv.ft_server_destroy(srv)
-        out[name] = serving.summarize(r, per_req)
-        nb = info.batches - info0.batches
-        out[name].update({"batches": int(nb),
-                          "mean_requests_per_batch": round((info.requests - info0.requests) / max(1, nb), 2),
-                          "max_batches_in_flight": int(info.max_batches_in_flight)})
+    out = {"workload": f"Poisson arrivals for {args.serve_seconds} s, n log-uniform [2^12, 2^24], R in {{3,5}}, "
+                       f"f32/f64 50/50, 40 GB budget, {len(specs)} resident payloads, 3 streams",
+           "batch_cap_bytes": 1 << 30}
+    for label, rate in (("at_20k_req_per_s", args.serve_rate), ("at_60k_req_per_s", 3 * args.serve_rate)):
+        reqs, _ = synth.cfg5_requests(duration_s=args.serve_seconds, rate=rate, pool=args.serve_pool)
+        arrivals = np.array([r.t_arrival for r in reqs])
+        payload = np.array([r.payload for r in reqs])
+        per_req = np.array([(specs[r.payload].R + 1) * r.n * (4 if r.dtype == "f32" else 8) for r in reqs])
+        res = {"offered_gb_per_s": round(float(per_req.sum()) / args.serve_seconds / 1e9, 1)}
+        for name, slots, cap in (("continuous_batching", 4096, 1 << 30), ("unbatched", 1, 0)):
+            cfg = fv.ft_server_config(int(40e9), slots, 3, 8, 0, cap)
+            srv = ctypes.c_void_p()
+            fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
+            try:
+                warm = min(len(reqs), 300)
+                serving.replay(srv, descs, arrivals[:warm] - arrivals[0], payload[:warm])
+                info0 = fv.ft_server_stats()
+                fv.ft_server_info(srv, ctypes.byref(info0))
+                r = serving.replay(srv, descs, arrivals, payload)
+                info = fv.ft_server_stats()
+                fv.ft_server_info(srv, ctypes.byref(info))
+            finally:
+                fv.ft_server_destroy(srv)
+            res[name] = serving.summarize(r, per_req)
+            nb = info.batches - info0.batches
+            res[name].update({"batches": int(nb),
+                              "mean_requests_per_batch": round((info.requests - info0.requests) / max(1, nb), 2),
+                              "max_batches_in_flight": int(info.max_batches_in_flight)})
+        out[label] = res
     del keep
     torch.cuda.empty_cache()
     return out

@@ -191,6 +191,10 @@ typedef struct ft_server_config {
     int32_t  streams;           /* batches in flight at once (1..8)               */
     int32_t  tile_blocks;       /* batched-kernel tile (0 = 8)                     */
     int32_t  max_inflight;      /* most admitted, not yet collected requests (0 = 65536) */
+    uint64_t max_batch_bytes;   /* a batch takes waiting requests (oldest first) while their
+                                   (R+1)*n*sizeof(dtype) bytes stay within this, and at least
+                                   one (0 = no limit): bounds how long a small request waits
+                                   for the large ones packed with it */
 } ft_server_config;
 
 typedef struct ft_result {

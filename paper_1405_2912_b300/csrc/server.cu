@@ -215,11 +215,18 @@ void worker_main(ft_server *s)
         std::vector<ftv::TaskArgs> args;
         sl.tickets.clear();
         bool any_user = false;
+        unsigned long long batch_bytes = 0;
         while (!s->pending.empty() && (int)args.size() < s->cfg.max_slots) {
             const unsigned long long tk = s->pending.front();
-            s->pending.pop_front();
             auto it = s->reqs.find(tk);
-            if (it == s->reqs.end()) continue;
+            if (it == s->reqs.end()) {
+                s->pending.pop_front();
+                continue;
+            }
+            if (!args.empty() && s->cfg.max_batch_bytes && batch_bytes + it->second.bytes > s->cfg.max_batch_bytes)
+                break;
+            s->pending.pop_front();
+            batch_bytes += it->second.bytes;
             args.push_back(it->second.args);
             sl.tickets.push_back(tk);
             any_user |= it->second.user_stats != nullptr;

@@ -64,7 +64,8 @@ class ft_server_config(ctypes.Structure):
                 ("max_slots", ctypes.c_int32),
                 ("streams", ctypes.c_int32),
                 ("tile_blocks", ctypes.c_int32),
-                ("max_inflight", ctypes.c_int32)]
+                ("max_inflight", ctypes.c_int32),
+                ("max_batch_bytes", ctypes.c_uint64)]
 
 
 class ft_result(ctypes.Structure):

@@ -171,3 +171,30 @@ def test_server_counters():
         assert info.inflight_requests == 0 and info.inflight_bytes == 0
     finally:
         fv.ft_server_destroy(srv)
+
+
+def test_batch_byte_cap():
+    from paper_1405_2912_b300 import ftvote as fv
+    p = _requests(k=1, seed=12)[0]
+    tasks = [DevTask(p) for _ in range(6)]
+    need = (p.R + 1) * p.n * p.itemsize
+    cfg = fv.ft_server_config(1 << 34, 4096, 1, 8, 0, 2 * need)
+    srv = ctypes.c_void_p()
+    fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
+    try:
+        fv.ft_server_pause(srv, 1)
+        tks = []
+        for t in tasks:
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(t.desc), ctypes.byref(tk)) == fv.FT_OK
+            tks.append(tk.value)
+        fv.ft_server_pause(srv, 0)
+        r = fv.ft_result()
+        for tk in tks:
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        # two requests' bytes per batch: 6 requests in 3 batches on the single stream
+        assert info.batches == 3 and info.requests == 6 and info.max_batches_in_flight == 1
+    finally:
+        fv.ft_server_destroy(srv)
