@@ -309,8 +309,10 @@ def run_ours(args, problem, ws, rank, local):
         digest = {"bytes_per_call": nbytes, "gb_per_s": round(nbytes / t_d / 1e9, 1),
                   "us_per_call": round(t_d * 1e6, 1), "matches_fused_digest": bool(torch.equal(dout, crc))}
     del reps, out, crc
-    batched = run_batched(args, dev, stream) if args.batched_tasks > 0 else None
-    serving = run_serving(args, dev) if args.serve_seconds > 0 else None
+    # the batched and serving forms are measured on a single-rank run (each is a
+    # whole-GPU workload of its own; a scaling run times the vote step only)
+    batched = run_batched(args, dev, stream) if args.batched_tasks > 0 and ws == 1 else None
+    serving = run_serving(args, dev) if args.serve_seconds > 0 and ws == 1 else None
     if rank != 0:
         return
     cpu = None
