@@ -39,6 +39,11 @@
  *     argument validation and launch errors; results are valid once the
  *     stream reaches the work.
  *   - No entry point throws, aborts or falls back to the CPU.
+ *   - ft_vote, ft_digest, ft_vote_many, ft_vote_batched, the registry and the
+ *     rating functions may be called from several host threads at once.  A
+ *     plan, a server or a checkpoint context is used by one thread at a time,
+ *     except ft_submit / ft_poll / ft_server_info / ft_server_pause, which
+ *     any thread may call concurrently.
  */
 #ifndef FTVOTE_H
 #define FTVOTE_H
@@ -152,6 +157,8 @@ int ft_vote_many(const ft_vote_desc *descs, int32_t n, ft_stream stream);
 /* The tuning the plan uses. */
 int ft_plan_tune(const ft_plan *plan, ft_tune *out);
 
+/* Free the plan.  Its replays must have completed (synchronize the streams
+ * they were launched on first). */
 int ft_plan_destroy(ft_plan *plan);
 
 /* ---- batched vote without any allocation ---- */
@@ -313,6 +320,7 @@ int ft_ckpt_sync(ft_ckpt *ckpt, const void *dev_buf, void *host_copy, ft_stream 
 int ft_ckpt_restore(ft_ckpt *ckpt, void *dev_buf, const void *host_copy, ft_stream stream,
                     uint64_t *blocks_copied);
 
+/* Free the context (sync and restore are synchronous, so nothing is in flight). */
 int ft_ckpt_destroy(ft_ckpt *ckpt);
 
 /* ---- fault-aware rating of processing units (Sec. IV.B) ---- */
