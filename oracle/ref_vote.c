@@ -16,7 +16,7 @@
  *   still count as equal, because CPU and GPU kernels order and round their
  *   arithmetic differently.
  *
- *   Readings taken where the paper is silent (each is listed in the design doc):
+ *   Readings taken where the paper is silent:
  *     eq(a,b), integers:  bit patterns equal.
  *     eq(a,b), floats, evaluated in the element's own precision with IEEE
  *       round-to-nearest, no fused multiply-add, no flush-to-zero:

@@ -1,4 +1,4 @@
-// registry.cpp -- value types of registered buffers and the DMR driver.
+// registry.cpp -- value types of registered buffers, and task duplication.
 //
 // In the paper's API an application registers each memory area with its value
 // type and access mode (dls_register_data(ptr, size, DLS_VT_FLOAT, "w"),
