@@ -198,3 +198,60 @@ def test_batch_byte_cap():
         assert info.batches == 3 and info.requests == 6 and info.max_batches_in_flight == 1
     finally:
         fv.ft_server_destroy(srv)
+
+
+def test_concurrent_clients():
+    """Four host threads submit and poll at once (the ctypes calls release the
+    GIL, so the server's locking is exercised for real); every result equals
+    the payload voted alone."""
+    import threading
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    probs = _requests(k=16, seed=21)
+    tasks = [DevTask(p) for p in probs]
+    for t in tasks:
+        fv.check(fv.ft_vote(ctypes.byref(t.desc), fv.stream_handle()), "ft_vote")
+    torch.cuda.synchronize()
+    alone = [fv.parse_stats(t.stats, p.R) for t, p in zip(tasks, probs)]
+    descs = []
+    for t in tasks:
+        d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+        d.stats = None
+        descs.append(d)
+    srv = _server(budget=1 << 33, max_slots=8, streams=3)
+    errors = []
+
+    def client(cid):
+        rng = np.random.default_rng(cid)
+        res = fv.ft_result()
+        tk = ctypes.c_uint64()
+        try:
+            for _ in range(150):
+                k = int(rng.integers(0, len(descs)))
+                while True:
+                    rc = fv.ft_submit(srv, ctypes.byref(descs[k]), ctypes.byref(tk))
+                    if rc == fv.FT_OK:
+                        break
+                    assert rc == fv.FT_EAGAIN
+                    time.sleep(0.0005)
+                assert fv.ft_poll(srv, tk.value, 30_000_000, ctypes.byref(res)) == fv.FT_OK
+                R = probs[k].R
+                got = {"mismatch": list(res.stats.mismatch)[:R], "first_mismatch": list(res.stats.first_mismatch)[:R],
+                       "no_majority": res.stats.no_majority, "first_no_majority": res.stats.first_no_majority}
+                assert got == alone[k], (cid, k)
+        except Exception as e:          # reported by the main thread
+            errors.append(repr(e))
+
+    try:
+        threads = [threading.Thread(target=client, args=(i,)) for i in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(timeout=120)
+        assert not any(th.is_alive() for th in threads)
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        assert info.completed == 600 and info.inflight_requests == 0
+    finally:
+        fv.ft_server_destroy(srv)
+    assert not errors, errors[:3]

@@ -117,3 +117,36 @@ def test_cfg3_full_size():
         got = gpu_vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
         assert_same(got, ref, p.R)
         assert got["mismatch"][3] >= (1 << 20) - 1024
+
+
+def test_vote_captured_in_a_user_graph():
+    """ft_vote (after one ordinary call has set up its kernel) can be recorded
+    into a caller's CUDA graph; replays vote the current contents of the
+    buffers, and equal the oracle."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    p = synth.cfg1(n=(1 << 18) + 11, flips=40)
+    dev = [torch.from_numpy(r).cuda() for r in p.replicas]
+    out, crc, st = fv.vote(dev, p.abs_tol, p.rel_tol)          # warm-up call outside the capture
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        fv.vote(dev, p.abs_tol, p.rel_tol, out=out, block_crc=crc, stats=st, stream=s)
+    for k in range(2):
+        # new contents between replays: replica 0 takes the flips of replica 2 on the second replay
+        host = [r.copy() for r in p.replicas]
+        if k == 1:
+            host[0] = host[2].copy()
+            for r, h in zip(dev, host):
+                r.copy_(torch.from_numpy(h))
+        out.zero_()
+        st.fill_(7)
+        g.replay()
+        torch.cuda.synchronize()
+        ref = oracle.vote(host, "f32", p.abs_tol, p.rel_tol)
+        assert out.cpu().numpy().tobytes() == ref["out"].tobytes()
+        assert np.array_equal(crc.cpu().numpy().view(np.uint32), ref["block_crc"])
+        s_ = fv.parse_stats(st, 3)
+        assert s_["mismatch"] == [int(x) for x in ref["mismatch"]]
+        assert s_["no_majority"] == ref["no_majority"]
