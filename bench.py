@@ -313,6 +313,7 @@ def run_ours(args, problem, ws, rank, local):
     # whole-GPU workload of its own; a scaling run times the vote step only)
     batched = run_batched(args, dev, stream) if args.batched_tasks > 0 and ws == 1 else None
     serving = run_serving(args, dev) if args.serve_seconds > 0 and ws == 1 else None
+    size_sweep = run_size_sweep(args, dev) if args.size_sweep and ws == 1 else None
     if rank != 0:
         return
     cpu = None
@@ -342,6 +343,7 @@ def run_ours(args, problem, ws, rank, local):
         "digest": digest,
         "batched": batched,
         "serving": serving,
+        "size_sweep": size_sweep,
     }
     print(json.dumps(line), flush=True)
 
@@ -470,6 +472,62 @@ def run_serving(args, dev):
     return out
 
 
+def run_size_sweep(args, dev):
+    """Voter time against result size, after the paper's comparison of its
+    single-thread, OpenMP and GPU voter kernels (Sec. V.A): R = 2 (DMR) f32
+    results of 1 KB to 256 MB, resident in each unit's memory (transfers
+    excluded, as in the paper).  GPU: median wall time of one synchronous
+    ft_vote.  CPU: the oracle on one thread and on all host cores (4 KiB-aligned
+    chunks), up to 64 MB."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    rng = np.random.default_rng(99)
+    rows = []
+    for kb in (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536, 262144):
+        n = kb * 256                          # f32 elements per replica
+        a = rng.standard_normal(n).astype(np.float32)
+        b = a.copy()
+        b[::97] = np.nextafter(b[::97], np.float32(np.inf))
+        p = synth.Problem([a, b], "f32", *synth.TOL["f32"])
+        reps = [torch.from_numpy(x).to(dev) for x in (a, b)]
+        out = torch.empty_like(reps[0])
+        crc = torch.empty(fv.n_blocks(4 * n), dtype=torch.int32, device=dev)
+        st = fv.new_stats(dev)
+        d = fv.make_desc(reps, out, crc, st, p.abs_tol, p.rel_tol)
+        pd = ctypes.byref(d)
+        sh = fv.stream_handle()
+        for _ in range(3):
+            fv.ft_vote(pd, sh)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(21):
+            t0 = time.perf_counter()
+            fv.ft_vote(pd, sh)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        row = {"kb_per_result": kb, "gpu_us": round(statistics.median(ts) * 1e6, 1)}
+        if kb <= 65536:
+            c1 = []
+            for _ in range(3 if kb <= 4096 else 1):
+                t0 = time.perf_counter()
+                oracle.vote([a, b], "f32", p.abs_tol, p.rel_tol)
+                c1.append(time.perf_counter() - t0)
+            row["cpu_1thread_us"] = round(min(c1) * 1e6, 1)
+            cn = [oracle_run(p, n, cores)[0] for _ in range(3 if kb <= 4096 else 1)]
+            row[f"cpu_{cores}threads_us"] = round(min(cn) * 1e6, 1)
+        rows.append(row)
+    fastest = []
+    for r in rows:
+        cand = {k[:-3]: v for k, v in r.items() if k.endswith("_us")}
+        fastest.append((r["kb_per_result"], min(cand, key=cand.get)))
+    return {"workload": "R=2 (DMR) f32 results with 1 ULP differences on 1 % of elements, resident in the "
+                        "voting unit's memory", "rows": rows,
+            "fastest_by_size_kb": fastest}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,6 +540,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1 << 26, help="elements per reference step")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
     ap.add_argument("--digest-reps", type=int, default=50, help="timed ft_digest calls on the voted buffer (0 = skip)")
+    ap.add_argument("--size-sweep", type=int, default=1, help="voter time against result size, GPU vs CPU (0 = skip)")
     ap.add_argument("--batched-tasks", type=int, default=4096, help="tasks of the batched workload (0 = skip)")
     ap.add_argument("--batched-reps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the request stream (0 = skip)")
