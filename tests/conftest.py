@@ -12,6 +12,16 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300, sm_103a)")
 
 
+@pytest.fixture(scope="session", autouse=True)
+def built_libraries():
+    """Build the CUDA library and the oracle if missing or stale (no-ops when
+    they are up to date), so that every test runs against current binaries."""
+    from paper_1405_2912_b300 import build
+    build.build()
+    import oracle
+    oracle.build()
+
+
 @pytest.fixture(scope="session")
 def oracle_lib():
     import oracle
