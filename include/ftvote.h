@@ -88,7 +88,8 @@ typedef struct ft_stats {
  *   out               device, n * sizeof(dtype) bytes, 16-byte aligned; must
  *                     not overlap any replica.
  *   block_crc         device, ceil(n * sizeof(dtype) / 4096) uint32 entries,
- *                     4-byte aligned, or NULL to skip the digest.
+ *                     4-byte aligned, or NULL when no digest is wanted (the
+ *                     vote is not faster without it).
  *   stats             device, one ft_stats, 8-byte aligned (required).
  *   abs_tol, rel_tol  float dtypes: 0 <= rel_tol <= 1 and 0 <= abs_tol with
  *                     abs_tol finite once rounded to the element type (a
