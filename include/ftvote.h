@@ -321,8 +321,53 @@ int ft_ckpt_sync(ft_ckpt *ckpt, const void *dev_buf, void *host_copy, ft_stream 
 int ft_ckpt_restore(ft_ckpt *ckpt, void *dev_buf, const void *host_copy, ft_stream stream,
                     uint64_t *blocks_copied);
 
+/* Forget the checkpoint's digests (the host copy was changed behind the
+ * context's back): the next sync or restore moves every block. */
+int ft_ckpt_forget(ft_ckpt *ckpt);
+
 /* Free the context (sync and restore are synchronous, so nothing is in flight). */
 int ft_ckpt_destroy(ft_ckpt *ckpt);
+
+/* ---- memory areas with a host and a device sibling (Sec. IV.A) ---- */
+
+/* The paper's memory manager keeps siblings of each registered area in the
+ * memories of the processing units, tags each with the version of the data it
+ * holds (a write access increases it by one), transfers data to a requesting
+ * unit only when its sibling is older than the newest one, and, in the
+ * fault-tolerant mode, makes sure that the version a kernel is about to
+ * overwrite still exists in another memory so that a faulty run can be rolled
+ * back.  An ft_area does this for one host and one device sibling; transfers
+ * move only the 4 KiB blocks whose CRC32C differs (see ft_ckpt).  Requests are
+ * synchronous.  An area is used by one thread at a time. */
+#define FT_MEM_HOST     0
+#define FT_MEM_DEVICE   1
+#define FT_ACCESS_READ  1
+#define FT_ACCESS_WRITE 2
+typedef struct ft_area ft_area;   /* library-owned */
+
+/* Register host_ptr (host memory, bytes long, caller-owned) as an area whose
+ * host sibling holds version 1; allocates the device sibling.  Returns FT_OK,
+ * FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
+int ft_area_create(ft_area **area, void *host_ptr, uint64_t bytes);
+
+/* Access to the sibling in `memory` (FT_MEM_HOST / FT_MEM_DEVICE) with
+ * `access` (FT_ACCESS_READ and/or FT_ACCESS_WRITE).  The sibling is first
+ * brought to the newest version if it is older or invalid.  For a write, the
+ * current version is first made to exist in the other memory too, and the
+ * sibling's version then increases by one (the caller writes it next).
+ * *ptr receives the sibling's address; *blocks_moved (may be NULL) the 4 KiB
+ * blocks transferred.  FT_EINVAL if both siblings were invalidated. */
+int ft_area_request(ft_area *area, int32_t memory, int32_t access, void **ptr, ft_stream stream,
+                    uint64_t *blocks_moved);
+
+/* A fault during a kernel that wrote the sibling in `memory` left it in an
+ * unknown state: drop it; the other sibling still holds the previous version. */
+int ft_area_invalidate(ft_area *area, int32_t memory);
+
+/* Version held by each sibling (0 = none / invalid). */
+int ft_area_versions(const ft_area *area, uint64_t *host_version, uint64_t *device_version);
+
+int ft_area_destroy(ft_area *area);
 
 /* ---- fault-aware rating of processing units (Sec. IV.B) ---- */
 

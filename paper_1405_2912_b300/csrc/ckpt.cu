@@ -255,10 +255,133 @@ int ft_ckpt_restore(ft_ckpt *c, void *dev_buf, const void *host_copy, ft_stream 
     return FT_OK;
 }
 
+int ft_ckpt_forget(ft_ckpt *c)
+{
+    if (!c) return FT_EINVAL;
+    c->have = false;
+    return FT_OK;
+}
+
 int ft_ckpt_destroy(ft_ckpt *c)
 {
     if (!c) return FT_EINVAL;
     ckpt_free(c);
+    return FT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Areas with a host and a device sibling (Sec. IV.A): each sibling carries the
+// version of the data it holds; a request brings the requested sibling up to
+// the newest version, moving only the 4 KiB blocks whose digest differs, and a
+// write request bumps its version.  Before a write, the previous version is
+// made to exist in the other memory too, so that a faulty run can be rolled
+// back from it (the fault-tolerant rule of Sec. IV.A / IV.C).
+// ---------------------------------------------------------------------------
+struct ft_area {
+    void *host = nullptr;              // caller's host memory (the host sibling)
+    void *dev = nullptr;               // device sibling (library-owned)
+    unsigned long long bytes = 0;
+    unsigned long long version[2] = {0, 0};
+    bool valid[2] = {false, false};
+    ft_ckpt *ck = nullptr;             // digests of the host sibling's content, as seen on the device
+};
+
+extern "C" {
+
+int ft_area_create(ft_area **out, void *host_ptr, uint64_t bytes)
+{
+    if (!out || !host_ptr || bytes == 0) return FT_EINVAL;
+    *out = nullptr;
+    ft_area *a = new (std::nothrow) ft_area();
+    if (!a) return FT_ENOMEM;
+    a->host = host_ptr;
+    a->bytes = bytes;
+    a->version[FT_MEM_HOST] = 1;
+    a->valid[FT_MEM_HOST] = true;
+    int rc = ft_ckpt_create(&a->ck, bytes, 0);
+    if (rc == FT_OK) {
+        const cudaError_t e = cudaMalloc(&a->dev, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = e == cudaErrorMemoryAllocation ? FT_ENOMEM : ftv::cuda_fail(e);
+        }
+    }
+    if (rc != FT_OK) {
+        if (a->ck) ft_ckpt_destroy(a->ck);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return FT_OK;
+}
+
+// Bring sibling m up to the newest version from the other one.
+static int area_refresh(ft_area *a, int m, cudaStream_t s, unsigned long long *moved)
+{
+    const int o = 1 - m;
+    uint64_t k = 0;
+    int rc = FT_OK;
+    if (m == FT_MEM_DEVICE) rc = ft_ckpt_restore(a->ck, a->dev, a->host, s, &k);
+    else rc = ft_ckpt_sync(a->ck, a->dev, a->host, s, &k);
+    if (rc != FT_OK) return rc;
+    a->version[m] = a->version[o];
+    a->valid[m] = true;
+    *moved += k;
+    return FT_OK;
+}
+
+int ft_area_request(ft_area *a, int32_t memory, int32_t access, void **ptr, ft_stream stream, uint64_t *blocks_moved)
+{
+    if (!a || !ptr || (memory != FT_MEM_HOST && memory != FT_MEM_DEVICE) ||
+        (access & ~(FT_ACCESS_READ | FT_ACCESS_WRITE)) || !access)
+        return FT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = memory, o = 1 - memory;
+    if (!a->valid[m] && !a->valid[o]) return FT_EINVAL;   // both siblings lost
+    unsigned long long moved = 0;
+    const unsigned long long newest =
+        std::max(a->valid[m] ? a->version[m] : 0ull, a->valid[o] ? a->version[o] : 0ull);
+    int rc = FT_OK;
+    if (!a->valid[m] || a->version[m] < newest) rc = area_refresh(a, m, s, &moved);
+    if (rc == FT_OK && (access & FT_ACCESS_WRITE)) {
+        // keep the version about to be overwritten in the other memory
+        if (!a->valid[o] || a->version[o] < a->version[m]) rc = area_refresh(a, o, s, &moved);
+        if (rc == FT_OK) {
+            a->version[m] += 1;
+            // the device side no longer knows the digests of a rewritten host copy
+            if (m == FT_MEM_HOST) ft_ckpt_forget(a->ck);
+        }
+    }
+    if (rc != FT_OK) return rc;
+    *ptr = m == FT_MEM_HOST ? a->host : a->dev;
+    if (blocks_moved) *blocks_moved = moved;
+    return FT_OK;
+}
+
+int ft_area_invalidate(ft_area *a, int32_t memory)
+{
+    if (!a || (memory != FT_MEM_HOST && memory != FT_MEM_DEVICE)) return FT_EINVAL;
+    a->valid[memory] = false;
+    if (memory == FT_MEM_HOST) ft_ckpt_forget(a->ck);
+    return FT_OK;
+}
+
+int ft_area_versions(const ft_area *a, uint64_t *host_version, uint64_t *device_version)
+{
+    if (!a) return FT_EINVAL;
+    if (host_version) *host_version = a->valid[FT_MEM_HOST] ? a->version[FT_MEM_HOST] : 0;
+    if (device_version) *device_version = a->valid[FT_MEM_DEVICE] ? a->version[FT_MEM_DEVICE] : 0;
+    return FT_OK;
+}
+
+int ft_area_destroy(ft_area *a)
+{
+    if (!a) return FT_EINVAL;
+    cudaFree(a->dev);
+    ft_ckpt_destroy(a->ck);
+    delete a;
     return FT_OK;
 }
 

@@ -133,6 +133,15 @@ ft_ckpt_create = _sig("ft_ckpt_create", ctypes.c_int, ctypes.POINTER(_P), ctypes
 ft_ckpt_sync = _sig("ft_ckpt_sync", ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64))
 ft_ckpt_restore = _sig("ft_ckpt_restore", ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64))
 ft_ckpt_destroy = _sig("ft_ckpt_destroy", ctypes.c_int, _P)
+ft_ckpt_forget = _sig("ft_ckpt_forget", ctypes.c_int, _P)
+FT_MEM_HOST, FT_MEM_DEVICE, FT_ACCESS_READ, FT_ACCESS_WRITE = 0, 1, 1, 2
+ft_area_create = _sig("ft_area_create", ctypes.c_int, ctypes.POINTER(_P), _P, ctypes.c_uint64)
+ft_area_request = _sig("ft_area_request", ctypes.c_int, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P), _P,
+                       ctypes.POINTER(ctypes.c_uint64))
+ft_area_invalidate = _sig("ft_area_invalidate", ctypes.c_int, _P, ctypes.c_int32)
+ft_area_versions = _sig("ft_area_versions", ctypes.c_int, _P, ctypes.POINTER(ctypes.c_uint64),
+                        ctypes.POINTER(ctypes.c_uint64))
+ft_area_destroy = _sig("ft_area_destroy", ctypes.c_int, _P)
 FT_PAPER_F32_REL_TOL = 1e-3
 ft_register_data = _sig("ft_register_data", ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
                         ctypes.c_double)

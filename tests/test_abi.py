@@ -108,3 +108,14 @@ def test_ckpt_argument_checks(fv):
     assert fv.ft_ckpt_sync(None, 0x1000, 0x2000, None, None) == fv.FT_EINVAL
     assert fv.ft_ckpt_restore(None, 0x1000, 0x2000, None, None) == fv.FT_EINVAL
     assert fv.ft_ckpt_destroy(None) == fv.FT_EINVAL
+
+
+def test_area_argument_checks(fv):
+    a = ctypes.c_void_p()
+    p = ctypes.c_void_p()
+    assert fv.ft_area_create(ctypes.byref(a), None, 100) == fv.FT_EINVAL
+    assert fv.ft_area_create(ctypes.byref(a), 0x1000, 0) == fv.FT_EINVAL
+    assert fv.ft_area_request(None, 0, 1, ctypes.byref(p), None, None) == fv.FT_EINVAL
+    assert fv.ft_area_invalidate(None, 0) == fv.FT_EINVAL
+    assert fv.ft_area_destroy(None) == fv.FT_EINVAL
+    assert fv.ft_ckpt_forget(None) == fv.FT_EINVAL
