@@ -1,12 +1,15 @@
 """Benchmark of the majority voter on the 256M-element f32 workload.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n ELEMS]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload f32x3-256M|f32x3-1M|f64x5-64M|i32x5-64M]
 
-One step = one ft_vote of R=3 replicas of n float32 (default n = 2^28, 1 GiB per
-replica): the whole hot path (load, compare, vote, store, statistics, CRC32C per
-4 KiB block).  The metric is voter GB/s with bytes = (R+1) * n * 4 (R reads + 1
-write).  Inputs (4 GiB) exceed the 126 MB L2, so no flush is needed between
-steps.  Prints one JSON line (rank 0).
+One step = one ft_vote of the workload, by default R=3 replicas of 2^28 float32
+(1 GiB per replica): the whole hot path (load, compare, vote, store,
+statistics, CRC32C per 4 KiB block).  The metric is voter GB/s with bytes =
+(R+1) * n * sizeof(element) (R reads + 1 write).  The default inputs (4 GiB)
+exceed the 126 MB L2, so no flush is needed between steps.  The same line
+carries the digest, batched, serving and size-sweep measurements.  Prints one
+JSON line (rank 0).
 
 --impl reference times the CPU oracle (the plain C voter under oracle/) on the
 host cores over a bounded sample of the same workload.
@@ -34,14 +37,36 @@ sys.path.insert(0, ROOT)
 from paper_1405_2912_b300 import synth  # noqa: E402
 
 METRIC = "voter input GB/s & % of HBM peak; batched tasks/s; p50/p99 vote latency"
-WORKLOAD = ("3 x 256M float32 replicas (lognormal sigma 2, random sign; +-1..4 ULP on 20% of "
-            "replica 1; bit flips at 1e-6/element in replica 2), abs_tol 1e-6, rel_tol 1e-5, "
-            "CRC32C per 4 KiB block of the voted buffer")
+WORKLOADS = {
+    "f32x3-256M": "3 x 256M float32 replicas (lognormal sigma 2, random sign; +-1..4 ULP on 20% of replica 1; "
+                  "bit flips at 1e-6/element in replica 2), abs_tol 1e-6, rel_tol 1e-5, CRC32C per 4 KiB block "
+                  "of the voted buffer",
+    "f32x3-1M": "3 x 1M float32 replicas (uniform [-1, 1]; +-1..2 ULP on 10% of replica 1; 100 bit flips in "
+                "replica 2), abs_tol 1e-6, rel_tol 1e-5, CRC32C per 4 KiB block",
+    "f64x5-64M": "5 x 64M float64 replicas (lognormal sigma 2; replica 3 wrong on a 1M-element block, bit flips "
+                 "at 1e-5 in replicas 1 and 4, 1024 tie sites), rel_tol 1e-12, CRC32C per 4 KiB block",
+    "i32x5-64M": "5 x 64M int32 replicas (uniform; replica 3 wrong on a 1M-element block, bit flips at 1e-5 in "
+                 "replicas 1 and 4, 1024 tie sites), bit-wise, CRC32C per 4 KiB block",
+}
+
+
+def make_problem(args):
+    """The workload of the timed step (the 256M-element f32 vote by default)."""
+    if args.workload == "f32x3-256M":
+        return synth.cfg2(n=args.n)
+    if args.workload == "f32x3-1M":
+        return synth.cfg1()
+    f64, i32 = synth.cfg3()
+    return f64 if args.workload == "f64x5-64M" else i32
+
+
 FALLBACK_HBM_GBS = 6400.0
 
 
 KERNEL_SOURCES = ("paper_1405_2912_b300/csrc/common.cuh", "paper_1405_2912_b300/csrc/vote.cu")
-TRAFFIC_FILE = "profiles/vote_f32_r3_256M_dram.txt"
+TRAFFIC_FILES = {"f32x3-256M": "profiles/vote_f32_r3_256M_dram.txt",
+                 "f64x5-64M": "profiles/vote_f64_r5_64M_dram.txt",
+                 "i32x5-64M": "profiles/vote_i32_r5_64M_dram.txt"}
 
 
 def kernel_sources_hash() -> str:
@@ -53,11 +78,13 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes (read + write) of one voter launch on this workload, from the
-    ncu capture recorded in TRAFFIC_FILE, if the kernel sources are still the
+def measured_traffic(workload="f32x3-256M"):
+    """DRAM bytes (read + write) of one voter launch on the workload, from the
+    ncu capture recorded in TRAFFIC_FILES, if the kernel sources are still the
     ones it was taken on; else None."""
-    path = os.path.join(ROOT, TRAFFIC_FILE)
+    if workload not in TRAFFIC_FILES:
+        return None
+    path = os.path.join(ROOT, TRAFFIC_FILES[workload])
     if not os.path.exists(path):
         return None
     kv = {}
@@ -183,9 +210,11 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def config_of(problem, ws):
-    return {"workload": WORKLOAD, "R": problem.R, "n": problem.n, "bytes_per_step": problem.bytes_moved,
-            "l2": "inputs (4 GiB per step) exceed the 126 MB L2; no flush",
+def config_of(problem, ws, workload):
+    nb = problem.bytes_moved
+    l2 = (f"inputs ({nb / 2**30:.2f} GiB per step) exceed the 126 MB L2; no flush" if nb > (126 << 20)
+          else f"inputs ({nb / 2**20:.0f} MiB per step) fit in L2")
+    return {"workload": WORKLOADS[workload], "R": problem.R, "n": problem.n, "bytes_per_step": nb, "l2": l2,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
 
 
@@ -205,8 +234,8 @@ def run_reference(args, problem):
     line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(problem, 1),
+            "scaling": "weak", "vs_baseline": None, "dtype": problem.dtype, "data": "synthetic",
+            "config": config_of(problem, 1, args.workload),
             "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -240,28 +269,26 @@ def run_ours(args, problem, ws, rank, local):
         fv.check(fv.ft_vote(pd, sh), "ft_vote")
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_start, ev_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = fv.ft_launch_count()
     barrier(ws)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
+        ev_start.record(stream)
         for k in range(args.steps):
-            starts[k].record(stream)
             fv.ft_vote(pd, sh)
-            ends[k].record(stream)
+        ev_end.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
     launches = fv.ft_launch_count() - launches0
     clocks = sampler.stop()
-    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]          # ms, per launch pair
-    elapsed = starts[0].elapsed_time(ends[-1]) / 1e3                  # s, whole timed region
+    elapsed = ev_start.elapsed_time(ev_end) / 1e3                      # s, whole timed region
     t_max = max_over_ranks(elapsed, ws)
     bytes_step = problem.bytes_moved
     value = bytes_step * args.steps * ws / t_max / 1e9
-    launch_ms = statistics.mean(per)
+    launch_ms = 1e3 * elapsed / args.steps      # back-to-back launches on one stream: the mean per ft_vote
     peak, peak_kind = peaks()
     achieved = bytes_step / (launch_ms / 1e3) / 1e9
 
@@ -326,15 +353,16 @@ def run_ours(args, problem, ws, rank, local):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": problem.dtype,
         "data": "synthetic",
-        "config": config_of(problem, ws),
+        "config": config_of(problem, ws, args.workload),
         "hbm_frac_of_8tbs_spec": round(value / ws / 8000.0, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "traffic": args.traffic if args.traffic is not None else (
-                         measured_traffic() if n == 1 << 28 else None),
-                     "kernel": "vote_kernel<F32,R=3> + stats reset (one ft_vote)"},
+                         measured_traffic(args.workload) if args.workload != "f32x3-256M" or n == 1 << 28
+                         else None),
+                     "kernel": f"vote_kernel<{problem.dtype},R={R}> + stats reset (one ft_vote)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -534,7 +562,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1 << 28, help="elements per replica")
+    ap.add_argument("--workload", default="f32x3-256M", choices=sorted(WORKLOADS),
+                    help="the timed vote (default: the 256M-element f32 vote)")
+    ap.add_argument("--n", type=int, default=1 << 28, help="elements per replica of the f32x3-256M workload")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1 << 28, help="elements the oracle votes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=1 << 26, help="elements per reference step")
@@ -553,7 +583,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        problem = synth.cfg2(n=args.n)
+        problem = make_problem(args)
         run_reference(args, problem)
         return 0
     if ws > 1:
@@ -561,7 +591,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    problem = synth.cfg2(n=args.n)
+    problem = make_problem(args)
     run_ours(args, problem, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
