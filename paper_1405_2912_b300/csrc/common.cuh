@@ -408,62 +408,6 @@ __device__ __forceinline__ void vote_elem(const typename Elem<K>::V (&x)[R], typ
     m = (~Ew & ((1u << R) - 1u)) | ((2 * best > R) ? 0u : (1u << R));
 }
 
-// Exact vote of one element, not inlined: the rare path of the kinds whose
-// fast path compares bits first.
-template <int K, int R>
-__device__ __noinline__ void vote_elem_call(typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
-                                            typename Elem<K>::V &y, uint32_t &m)
-{
-    vote_elem<K, R>(x, c, y, m);
-}
-
-// Fast form: the winner's bits, and `flag` raised whenever the element may
-// have a mismatch or no majority (a superset; the exact statistics are then
-// recomputed with vote_elem).
-//   f32:         R = 3 closed form, other R the exact form, both branch-free
-//                (ULP-level disagreements are common in float results);
-//   integers:    R = 3 closed form; other R: equal bits in all replicas give
-//                replica 0 at once, anything else takes the exact form;
-//   f64:         equal bits first for every R (FP64 arithmetic is slow).
-template <int K, int R>
-__device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
-                                          typename Elem<K>::V &y, bool &flag)
-{
-    using E = Elem<K>;
-    constexpr bool kClosed3 = (R == 3) && !E::kBitsFirst;
-    constexpr bool kBitsPath = E::kBitsFirst || (K != K_F32 && !kClosed3);
-    if constexpr (kClosed3) {
-        // supports (1+e01+e02, 1+e01+e12, 1+e02+e12): replica 1 wins iff
-        // e12 and not e02; replica 2 iff e02, e12 and not e01; else replica 0.
-        // A mismatch or a missing majority needs not (e01 and e02), except in
-        // the non-transitive cases, which only raise the flag.
-        const typename E::P p0 = E::prep(x[0], c), p1 = E::prep(x[1], c), p2 = E::prep(x[2], c);
-        const bool e01 = E::eq(p0, p1, c), e02 = E::eq(p0, p2, c), e12 = E::eq(p1, p2, c);
-        const bool w1 = e12 & !e02;
-        const bool w2 = e02 & e12 & !e01;
-        y = w2 ? x[2] : (w1 ? x[1] : x[0]);
-        flag |= !(e01 & e02);
-    } else if constexpr (kBitsPath) {
-        bool same = true;
-#pragma unroll
-        for (int r = 1; r < R; ++r) same &= (x[r] == x[0]);
-        if (same) {
-            y = x[0];
-        } else {
-            typename E::V xc[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) xc[r] = x[r];
-            uint32_t m;
-            vote_elem_call<K, R>(xc, c, y, m);
-            flag |= (m != 0);
-        }
-    } else {
-        uint32_t m;
-        vote_elem<K, R>(x, c, y, m);
-        flag |= (m != 0);
-    }
-}
-
 // Per-lane statistics: counts and first indices for the R replicas and, at
 // index R, for elements without a majority.
 template <int R>
@@ -574,27 +518,132 @@ struct VotePolicy {
     static constexpr int kWarps = kPrefetch ? 12 : 16;
 };
 
-// Exact statistics of the elements of lane `lane`'s vectors j0 .. j0+JB-1 of
-// block b, recomputed from global memory (rare path).
-template <int K, int R, int JB>
-__device__ __noinline__ void exact_stats(const TaskArgs &a, unsigned long long b, int j0, int lane, LaneStats<R> &st)
+// Which fast form a (kind, R) takes in the full blocks.
+//   R = 3 closed form (f32 and the bit-compared integers): branch-free;
+//   f32, other R: the exact form, branch-free (ULP-level disagreements are
+//     common in float results, so the float rule runs for every element);
+//   integers, other R, and f64 for every R: equal bits in all replicas give
+//     replica 0 at once; anything else takes the exact form out of line
+//     (FP64 arithmetic is slow on this part).
+template <int K, int R>
+constexpr bool kClosed3 = (R == 3) && !Elem<K>::kBitsFirst;
+template <int K, int R>
+constexpr bool kBitsPath = Elem<K>::kBitsFirst || (K != K_F32 && !kClosed3<K, R>);
+
+// The rare paths, kept out of line so that they do not shape the fast path's
+// register allocation.  Each adds the mismatches of one or more elements to
+// the lane's statistics; nothing is reloaded from memory.
+template <int R>
+__device__ __noinline__ void record_elem(LaneStats<R> &st, uint32_t m, unsigned long long idx)
+{
+    st.add_one(m, idx);
+}
+
+template <int K, int R>
+__device__ __noinline__ void vote_elem_record(typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
+                                              typename Elem<K>::V &y, LaneStats<R> &st, unsigned long long idx)
+{
+    uint32_t m;
+    vote_elem<K, R>(x, c, y, m);
+    if (m) st.add_one(m, idx);
+}
+
+// Statistics of the R = 3 closed form for one sub-batch of a lane, from the
+// pairwise comparisons as bit masks: bit k of n01, n02, n12 is set when the
+// pair (0,1), (0,2), (1,2) of element k is NOT equal.  Element k is element
+// idx0 + (k / P) * 32 * P + k % P of the task (P elements per 16-byte vector,
+// a lane's vectors 32 apart), which grows with k, so a quantity's first index
+// is that of its lowest set bit.  With e_rq the equalities, the supports are
+// 1+e01+e02, 1+e01+e12, 1+e02+e12 and the first maximum wins: replica 1 iff
+// e12 and not e02, replica 2 iff e02 and e12 and not e01, else replica 0.
+// Replica r mismatches iff it is not equal to the winner; the winner's
+// support is 1 (no majority) iff no pair is equal.
+template <int P>
+__device__ __forceinline__ void closed3_stats(uint64_t n01, uint64_t n02, uint64_t n12, unsigned long long idx0,
+                                              LaneStats<3> &st)
+{
+    const uint64_t w1 = ~n12 & n02;
+    const uint64_t w2 = ~n02 & ~n12 & n01;
+    const uint64_t w0 = ~(w1 | w2);
+    const uint64_t q[4] = {(w1 & n01) | (w2 & n02), (w0 & n01) | (w2 & n12), (w0 & n02) | (w1 & n12),
+                           n01 & n02 & n12};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (!q[r]) continue;
+        const int k = __ffsll((long long)q[r]) - 1;
+        const unsigned long long i = idx0 + (unsigned long long)(k / P) * (32ull * P) + (unsigned long long)(k % P);
+        st.cnt[r] += (unsigned long long)__popcll(q[r]);
+        st.first[r] = st.first[r] < i ? st.first[r] : i;
+    }
+}
+
+// Rare path of the R = 3 closed form: the sub-batch (vectors j0 .. j0+JB-1 of
+// the lane in the block at byte offset boff) had an element where replica 0
+// disagrees with another replica.  The sub-batch is read again from the
+// replicas (one round trip, all vectors in flight; the output never overlaps
+// a replica) and its pairwise comparisons turned into statistics.
+template <int K, int JB>
+__device__ __noinline__ void closed3_rare(const TaskArgs &a, unsigned long long boff, int lane, int j0,
+                                          unsigned long long idx0, LaneStats<3> &st)
 {
     using E = Elem<K>;
-    constexpr int kPerVec = 16 / E::kSize;
-    constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
+    constexpr int P = 16 / E::kSize;
     const typename E::Ctx c = E::ctx(a.abs_tol, a.rel_tol);
-    for (int jj = 0; jj < JB; ++jj) {
-        const unsigned long long vi = (unsigned long long)(lane + 32 * (j0 + jj));
-        for (int e = 0; e < kPerVec; ++e) {
-            const unsigned long long off = b * kBlockBytes + vi * 16 + (unsigned long long)e * E::kSize;
-            typename E::V x[R];
+    uint4 v[3][JB];
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = load_elem<K>(a.rep[r] + off);
-            typename E::V y;
-            uint32_t m;
-            vote_elem<K, R>(x, c, y, m);
-            if (m) st.add_one(m, b * kEpb + vi * kPerVec + e);
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj)
+            v[r][jj] = reinterpret_cast<const uint4 *>(a.rep[r] + boff)[lane + 32 * (j0 + jj)];
+    uint64_t n01 = 0, n02 = 0, n12 = 0;
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj)
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+            const uint64_t bit = 1ull << (jj * P + e);
+            const typename E::P p0 = E::prep(E::get(v[0][jj], e), c), p1 = E::prep(E::get(v[1][jj], e), c),
+                                p2 = E::prep(E::get(v[2][jj], e), c);
+            n01 |= E::eq(p0, p1, c) ? 0ull : bit;
+            n02 |= E::eq(p0, p2, c) ? 0ull : bit;
+            n12 |= E::eq(p1, p2, c) ? 0ull : bit;
         }
+    closed3_stats<P>(n01, n02, n12, idx0, st);
+}
+
+// Fast vote of element k of a lane's sub-batch (element idx of the task):
+// the winner's bits in y.  The closed form sets bit k of `flagged` where
+// replica 0 disagrees with replica 1 or 2 (only such elements can have a
+// mismatch or lack a majority); the other forms record a mismatch into st at
+// once, out of line.
+template <int K, int R>
+__device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
+                                          typename Elem<K>::V &y, int k, uint64_t &flagged, LaneStats<R> &st,
+                                          unsigned long long idx)
+{
+    using E = Elem<K>;
+    if constexpr (kClosed3<K, R>) {
+        const typename E::P p0 = E::prep(x[0], c), p1 = E::prep(x[1], c), p2 = E::prep(x[2], c);
+        const bool e01 = E::eq(p0, p1, c), e02 = E::eq(p0, p2, c), e12 = E::eq(p1, p2, c);
+        const bool w1 = e12 & !e02;
+        const bool w2 = e02 & e12 & !e01;
+        y = w2 ? x[2] : (w1 ? x[1] : x[0]);
+        flagged |= (e01 & e02) ? 0ull : (1ull << k);
+    } else if constexpr (kBitsPath<K, R>) {
+        bool same = true;
+#pragma unroll
+        for (int r = 1; r < R; ++r) same &= (x[r] == x[0]);
+        if (same) {
+            y = x[0];
+        } else {
+            typename E::V xc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) xc[r] = x[r];
+            vote_elem_record<K, R>(xc, c, y, st, idx);
+        }
+    } else {
+        uint32_t m;
+        vote_elem<K, R>(x, c, y, m);
+        if (m) record_elem<R>(st, m, idx);
     }
 }
 
@@ -620,6 +669,8 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     using V = typename E::V;
     constexpr int kPerVec = 16 / E::kSize;
     constexpr int JB = kSubBatch<K, R>;                      // vectors per lane per sub-batch
+    constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
+    static_assert(!kClosed3<K, R> || JB * kPerVec <= 64, "the closed form's masks hold one bit per element of a sub-batch");
     const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
     const unsigned long long boff = b * kBlockBytes;
     if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);
@@ -632,7 +683,8 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj)
                 v[r][jj] = ld_stream(reinterpret_cast<const uint4 *>(a.rep[r] + boff) + lane + 32 * (j0 + jj));
-        bool flag = false;
+        uint64_t flagged = 0;
+        const unsigned long long idx0 = b * kEpb + (unsigned long long)(lane + 32 * j0) * kPerVec;
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
             uint4 yv = v[0][jj];
@@ -642,14 +694,16 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
 #pragma unroll
                 for (int r = 0; r < R; ++r) x[r] = E::get(v[r][jj], e);
                 V y;
-                vote_fast<K, R>(x, ctx, y, flag);
+                vote_fast<K, R>(x, ctx, y, jj * kPerVec + e, flagged, st,
+                                idx0 + (unsigned long long)(jj * 32 * kPerVec + e));
                 E::set(yv, e, y);
             }
             const int vi = lane + 32 * (j0 + jj);
             __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
             tile[tile_index(vi)] = yv;
         }
-        if (flag) exact_stats<K, R, JB>(a, b, j0, lane, st);
+        if constexpr (kClosed3<K, R>)
+            if (flagged) closed3_rare<K, JB>(a, boff, lane, j0, idx0, st);
     }
     __syncwarp();
     const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);

@@ -175,3 +175,64 @@ def test_vote_without_digest(dtype, R):
         ref = oracle.vote(reps, dtype, *tol)
         got["block_crc"] = ref["block_crc"]
         assert_same(got, ref, R)
+
+
+# Positions on a line, in units of h = 0.75 * abs_tol, for each pattern of
+# (x0 != x1, x0 != x2, x1 != x2) under an absolute tolerance: neighbours one
+# h apart are equal, two h apart are not.  The three patterns with exactly one
+# unequal pair are the non-transitive ones.
+_PATTERN_POS = {(0, 0, 0): (0, 0, 0), (1, 0, 0): (0, 2, 1), (0, 1, 0): (0, 1, 2), (0, 0, 1): (1, 0, 2),
+                (1, 1, 0): (0, 10, 10), (1, 0, 1): (0, 10, 0), (0, 1, 1): (0, 0, 10), (1, 1, 1): (0, 10, 20)}
+
+
+def _dense_r3(dtype, n, seed):
+    """R = 3 replicas in which every element takes one of the eight pair
+    patterns at random (floats), or one of the five that bitwise equality
+    allows (integers), so most elements carry a mismatch or lack a majority."""
+    rng = np.random.default_rng(seed)
+    t = oracle.NP_OF[dtype]
+    if dtype in ("f32", "f64"):
+        abs_tol = 1e-3
+        pats = list(_PATTERN_POS)
+        pos = np.array([_PATTERN_POS[p] for p in pats], dtype=t)[rng.integers(0, len(pats), size=n)]
+        base = (rng.integers(-50, 50, size=n) * 100).astype(t) * t(abs_tol)
+        reps = [base + pos[:, r] * t(0.75 * abs_tol) for r in range(3)]
+        return [np.ascontiguousarray(x, dtype=t) for x in reps], (abs_tol, 0.0)
+    info = np.iinfo(t)
+    vals = [rng.integers(info.min, info.max, size=n, dtype=t, endpoint=True) for _ in range(3)]
+    which = rng.integers(0, 5, size=n)              # 0: all equal, 1..3: replica which-1 differs, 4: all differ
+    reps = [vals[0].copy() for _ in range(3)]
+    for r in range(3):
+        sel = (which == r + 1) | ((which == 4) & (r > 0))
+        reps[r][sel] = vals[r][sel] if r > 0 else vals[1][sel]
+    return reps, (0.0, 0.0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "i32", "u8", "i64"])
+def test_dense_disagreement_r3(dtype):
+    """Mismatches and missing majorities at most elements (every pattern of the
+    three pairwise comparisons, non-transitive ones included): the statistics
+    of the R = 3 closed form's rare path, across several blocks and a tail."""
+    for k, n in enumerate((7, 1025, 65536 + 13, 300_001)):
+        reps, tol = _dense_r3(dtype, n, seed=500 + k)
+        ref = oracle.vote(reps, dtype, *tol)
+        if n > 1000:
+            assert ref["no_majority"] > 0 and min(ref["mismatch"]) > 0
+        assert_same(gpu_vote(reps, dtype, *tol), ref, 3)
+
+
+@pytest.mark.parametrize("dtype,R", [("f32", 3), ("f32", 5), ("f64", 3), ("i32", 3), ("i32", 5), ("u8", 3)])
+def test_one_replica_wrong_everywhere(dtype, R):
+    """Replica 1 disagrees with the others at every element (a unit that
+    returns garbage): every element is a mismatch of replica 1."""
+    rng = np.random.default_rng(R)
+    n = 4096 * 37 + 5
+    reps, tol = _random_problem(dtype, R, n, seed=9 + R)
+    reps = [np.ascontiguousarray(reps[0]) for _ in range(R)]
+    bad = reps[1].view(np.uint8).copy()
+    bad ^= rng.integers(1, 256, size=bad.size, dtype=np.uint8) | np.uint8(0x80) if dtype == "u8" else \
+        np.tile(np.array([0, 0, 0, 0x40] if reps[1].dtype.itemsize == 4 else [0] * 7 + [0x40], dtype=np.uint8), n)
+    reps[1] = bad.view(reps[0].dtype)
+    ref = oracle.vote(reps, dtype, *tol)
+    assert int(ref["mismatch"][1]) == n
+    assert_same(gpu_vote(reps, dtype, *tol), ref, R)
