@@ -503,7 +503,7 @@ __device__ __forceinline__ void store_elem(uint8_t *p, typename Elem<K>::V v)
 // R = 5..6 of the kinds with the equal-bits fast path measured the same as 2
 // on the 5 x 64M f64 / i32 workloads and spilled.)
 template <int K, int R>
-constexpr int kSubBatch = (R <= 2) ? 8 : (R <= 4 ? 4 : 2);
+constexpr int kSubBatch = (K == K_B1 && R <= 2) ? 4 : ((R <= 2) ? 8 : (R <= 4 ? 4 : 2));
 
 // Launch shape of the voter kernels for one (kind, R), chosen by measurement
 // on B300 (3 x 256M f32; 5 x 64M f64 and i32): warps per CTA (one CTA per SM)
@@ -519,26 +519,45 @@ struct VotePolicy {
 };
 
 // Which fast form a (kind, R) takes in the full blocks.
-//   R = 3 closed form (f32 and the bit-compared integers): branch-free;
-//   f32, other R: the exact form, branch-free (ULP-level disagreements are
-//     common in float results, so the float rule runs for every element);
-//   integers, other R, and f64 for every R: equal bits in all replicas give
-//     replica 0 at once; anything else takes the exact form out of line
-//     (FP64 arithmetic is slow on this part).
+//   F_CLOSED2  R = 2, every kind: replica 0 always wins (equal supports tie
+//              to the lower index); replica 1 mismatches, and there is no
+//              majority, exactly where the pair is not equal.  One comparison
+//              per element; the statistics come from a bit mask.
+//   F_CLOSED3  R = 3, f32 and the bit-compared integers: the winner in closed
+//              form from the three pairwise comparisons, branch-free; a
+//              sub-batch where replica 0 disagrees with another replica is
+//              read again for its statistics.
+//   F_EQ0      f32, R >= 4: replica 0 equal to every other replica (support R)
+//              wins with no mismatch, R - 1 comparisons per element; any
+//              other sub-batch is read again and voted in the exact form.
+//   F_BITS     integers with R >= 4 and f64 with R >= 3: equal bits in all
+//              replicas give replica 0 at once; an element whose bits differ
+//              takes the exact form out of line (FP64 arithmetic is slow on
+//              this part, so it runs only there).
+// ULP-level disagreements are common in float results, which is why the f32
+// forms apply the tolerance rule to every element rather than bits first.
+enum Form { F_CLOSED2, F_CLOSED3, F_EQ0, F_BITS };
 template <int K, int R>
-constexpr bool kClosed3 = (R == 3) && !Elem<K>::kBitsFirst;
-template <int K, int R>
-constexpr bool kBitsPath = Elem<K>::kBitsFirst || (K != K_F32 && !kClosed3<K, R>);
+constexpr Form kForm = (R == 2) ? F_CLOSED2
+                     : (R == 3 && !Elem<K>::kBitsFirst) ? F_CLOSED3
+                     : (K == K_F32 ? F_EQ0 : F_BITS);
 
-// The rare paths, kept out of line so that they do not shape the fast path's
-// register allocation.  Each adds the mismatches of one or more elements to
-// the lane's statistics; nothing is reloaded from memory.
-template <int R>
-__device__ __noinline__ void record_elem(LaneStats<R> &st, uint32_t m, unsigned long long idx)
+// Adds the elements of bit mask q (bit k: element idx0 + (k / P) * 32 * P +
+// k % P, P elements per 16-byte vector, a lane's vectors 32 apart) to
+// quantity r of the lane statistics.  The index grows with k, so the first
+// index is that of the lowest set bit.
+template <int P, int R>
+__device__ __forceinline__ void add_mask(LaneStats<R> &st, int r, uint64_t q, unsigned long long idx0)
 {
-    st.add_one(m, idx);
+    if (!q) return;
+    const int k = __ffsll((long long)q) - 1;
+    const unsigned long long i = idx0 + (unsigned long long)(k / P) * (32ull * P) + (unsigned long long)(k % P);
+    st.cnt[r] += (unsigned long long)__popcll(q);
+    st.first[r] = st.first[r] < i ? st.first[r] : i;
 }
 
+// The rare paths are kept out of line so that they do not shape the fast
+// path's register allocation.
 template <int K, int R>
 __device__ __noinline__ void vote_elem_record(typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
                                               typename Elem<K>::V &y, LaneStats<R> &st, unsigned long long idx)
@@ -546,6 +565,14 @@ __device__ __noinline__ void vote_elem_record(typename Elem<K>::V (&x)[R], typen
     uint32_t m;
     vote_elem<K, R>(x, c, y, m);
     if (m) st.add_one(m, idx);
+}
+
+// R = 2: bit k of n01 set where the pair of element k is not equal.
+template <int P>
+__device__ __noinline__ void closed2_stats(uint64_t n01, unsigned long long idx0, LaneStats<2> &st)
+{
+    add_mask<P, 2>(st, 1, n01, idx0);
+    add_mask<P, 2>(st, 2, n01, idx0);
 }
 
 // Statistics of the R = 3 closed form for one sub-batch of a lane, from the
@@ -565,16 +592,10 @@ __device__ __forceinline__ void closed3_stats(uint64_t n01, uint64_t n02, uint64
     const uint64_t w1 = ~n12 & n02;
     const uint64_t w2 = ~n02 & ~n12 & n01;
     const uint64_t w0 = ~(w1 | w2);
-    const uint64_t q[4] = {(w1 & n01) | (w2 & n02), (w0 & n01) | (w2 & n12), (w0 & n02) | (w1 & n12),
-                           n01 & n02 & n12};
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        if (!q[r]) continue;
-        const int k = __ffsll((long long)q[r]) - 1;
-        const unsigned long long i = idx0 + (unsigned long long)(k / P) * (32ull * P) + (unsigned long long)(k % P);
-        st.cnt[r] += (unsigned long long)__popcll(q[r]);
-        st.first[r] = st.first[r] < i ? st.first[r] : i;
-    }
+    add_mask<P, 3>(st, 0, (w1 & n01) | (w2 & n02), idx0);
+    add_mask<P, 3>(st, 1, (w0 & n01) | (w2 & n12), idx0);
+    add_mask<P, 3>(st, 2, (w0 & n02) | (w1 & n12), idx0);
+    add_mask<P, 3>(st, 3, n01 & n02 & n12, idx0);
 }
 
 // Rare path of the R = 3 closed form: the sub-batch (vectors j0 .. j0+JB-1 of
@@ -610,25 +631,95 @@ __device__ __noinline__ void closed3_rare(const TaskArgs &a, unsigned long long 
     closed3_stats<P>(n01, n02, n12, idx0, st);
 }
 
+// Rare path of F_EQ0: in the sub-batch (vectors j0 .. j0+JB-1 of the lane in
+// the block at byte offset boff) some element's replica 0 disagrees with
+// another replica.  The sub-batch is read again (one round trip; the output
+// never overlaps a replica) and voted in the exact form; its voted vectors
+// replace the fast form's in the output and in the digest tile.
+template <int K, int R, int JB>
+__device__ __noinline__ void eq0_rare(const TaskArgs &a, unsigned long long boff, int lane, int j0,
+                                      unsigned long long idx0, uint4 *tile, LaneStats<R> &st)
+{
+    using E = Elem<K>;
+    constexpr int P = 16 / E::kSize;
+    const typename E::Ctx c = E::ctx(a.abs_tol, a.rel_tol);
+    uint4 v[R][JB];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj)
+            v[r][jj] = reinterpret_cast<const uint4 *>(a.rep[r] + boff)[lane + 32 * (j0 + jj)];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) {
+        uint4 yv;
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+            typename E::V x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = E::get(v[r][jj], e);
+            typename E::V y;
+            uint32_t m;
+            vote_elem<K, R>(x, c, y, m);
+            E::set(yv, e, y);
+            if (m) st.add_one(m, idx0 + (unsigned long long)(jj * 32 * P + e));
+        }
+        const int vi = lane + 32 * (j0 + jj);
+        __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
+        tile[tile_index(vi)] = yv;
+    }
+}
+
+// u8, R = 3: the closed form on four bytes at a time.  __vcmpeq4 gives 0xFF
+// in each byte where two words agree; the byte masks then select replica 1
+// (e12 and not e02), replica 2 (e02 and e12 and not e01) or replica 0, as in
+// the element form.  `flagged` is set when a byte of replica 0 disagrees with
+// replica 1 or 2.
+__device__ __forceinline__ uint4 vote_b1_closed3(const uint4 &a, const uint4 &b, const uint4 &c, uint64_t &flagged)
+{
+    uint4 y;
+    uint32_t nf = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t x0 = (&a.x)[w], x1 = (&b.x)[w], x2 = (&c.x)[w];
+        const uint32_t e01 = __vcmpeq4(x0, x1), e02 = __vcmpeq4(x0, x2), e12 = __vcmpeq4(x1, x2);
+        const uint32_t s1 = e12 & ~e02, s2 = e02 & e12 & ~e01;
+        (&y.x)[w] = (x0 & ~(s1 | s2)) | (x1 & s1) | (x2 & s2);
+        nf |= ~(e01 & e02);
+    }
+    flagged |= nf ? 1ull : 0ull;
+    return y;
+}
+
 // Fast vote of element k of a lane's sub-batch (element idx of the task):
-// the winner's bits in y.  The closed form sets bit k of `flagged` where
-// replica 0 disagrees with replica 1 or 2 (only such elements can have a
-// mismatch or lack a majority); the other forms record a mismatch into st at
-// once, out of line.
+// the winner's bits in y, or replica 0's where the rare path of the form
+// decides.  F_CLOSED2, F_CLOSED3 and F_EQ0 set bit k of `flagged` where the
+// element may have a mismatch or lack a majority; F_BITS records a mismatch
+// into st at once, out of line.
 template <int K, int R>
 __device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
                                           typename Elem<K>::V &y, int k, uint64_t &flagged, LaneStats<R> &st,
                                           unsigned long long idx)
 {
     using E = Elem<K>;
-    if constexpr (kClosed3<K, R>) {
+    constexpr Form F = kForm<K, R>;
+    if constexpr (F == F_CLOSED2) {
+        y = x[0];
+        flagged |= E::eq(E::prep(x[0], c), E::prep(x[1], c), c) ? 0ull : (1ull << k);
+    } else if constexpr (F == F_CLOSED3) {
         const typename E::P p0 = E::prep(x[0], c), p1 = E::prep(x[1], c), p2 = E::prep(x[2], c);
         const bool e01 = E::eq(p0, p1, c), e02 = E::eq(p0, p2, c), e12 = E::eq(p1, p2, c);
         const bool w1 = e12 & !e02;
         const bool w2 = e02 & e12 & !e01;
         y = w2 ? x[2] : (w1 ? x[1] : x[0]);
         flagged |= (e01 & e02) ? 0ull : (1ull << k);
-    } else if constexpr (kBitsPath<K, R>) {
+    } else if constexpr (F == F_EQ0) {
+        const typename E::P p0 = E::prep(x[0], c);
+        bool all = true;
+#pragma unroll
+        for (int r = 1; r < R; ++r) all &= E::eq(p0, E::prep(x[r], c), c);
+        y = x[0];
+        flagged |= all ? 0ull : (1ull << k);
+    } else {
         bool same = true;
 #pragma unroll
         for (int r = 1; r < R; ++r) same &= (x[r] == x[0]);
@@ -640,10 +731,6 @@ __device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typ
             for (int r = 0; r < R; ++r) xc[r] = x[r];
             vote_elem_record<K, R>(xc, c, y, st, idx);
         }
-    } else {
-        uint32_t m;
-        vote_elem<K, R>(x, c, y, m);
-        if (m) record_elem<R>(st, m, idx);
     }
 }
 
@@ -670,7 +757,8 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     constexpr int kPerVec = 16 / E::kSize;
     constexpr int JB = kSubBatch<K, R>;                      // vectors per lane per sub-batch
     constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
-    static_assert(!kClosed3<K, R> || JB * kPerVec <= 64, "the closed form's masks hold one bit per element of a sub-batch");
+    constexpr Form F = kForm<K, R>;
+    static_assert(F == F_BITS || JB * kPerVec <= 64, "`flagged` holds one bit per element of a sub-batch");
     const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
     const unsigned long long boff = b * kBlockBytes;
     if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);
@@ -688,22 +776,42 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
             uint4 yv = v[0][jj];
+            if constexpr (K == K_B1 && R == 3) {
+                yv = vote_b1_closed3(v[0][jj], v[1][jj], v[2][jj], flagged);
+            } else {
+                // kinds compared bits first (all but f32): a vector equal in
+                // all replicas is replica 0's, with no mismatch
+                constexpr bool kPre = (K != K_F32) && F != F_CLOSED3;
+                bool differ = !kPre;
+                if constexpr (kPre) {
 #pragma unroll
-            for (int e = 0; e < kPerVec; ++e) {
-                V x[R];
+                    for (int r = 1; r < R; ++r)
+                        differ |= ((v[r][jj].x ^ v[0][jj].x) | (v[r][jj].y ^ v[0][jj].y) |
+                                   (v[r][jj].z ^ v[0][jj].z) | (v[r][jj].w ^ v[0][jj].w)) != 0u;
+                }
+                if (differ) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) x[r] = E::get(v[r][jj], e);
-                V y;
-                vote_fast<K, R>(x, ctx, y, jj * kPerVec + e, flagged, st,
-                                idx0 + (unsigned long long)(jj * 32 * kPerVec + e));
-                E::set(yv, e, y);
+                    for (int e = 0; e < kPerVec; ++e) {
+                        V x[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) x[r] = E::get(v[r][jj], e);
+                        V y;
+                        vote_fast<K, R>(x, ctx, y, jj * kPerVec + e, flagged, st,
+                                        idx0 + (unsigned long long)(jj * 32 * kPerVec + e));
+                        E::set(yv, e, y);
+                    }
+                }
             }
             const int vi = lane + 32 * (j0 + jj);
             __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
             tile[tile_index(vi)] = yv;
         }
-        if constexpr (kClosed3<K, R>)
+        if constexpr (F == F_CLOSED2)
+            if (flagged) closed2_stats<kPerVec>(flagged, idx0, st);
+        if constexpr (F == F_CLOSED3)
             if (flagged) closed3_rare<K, JB>(a, boff, lane, j0, idx0, st);
+        if constexpr (F == F_EQ0)
+            if (flagged) eq0_rare<K, R, JB>(a, boff, lane, j0, idx0, tile, st);
     }
     __syncwarp();
     const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);

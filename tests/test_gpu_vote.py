@@ -236,3 +236,34 @@ def test_one_replica_wrong_everywhere(dtype, R):
     ref = oracle.vote(reps, dtype, *tol)
     assert int(ref["mismatch"][1]) == n
     assert_same(gpu_vote(reps, dtype, *tol), ref, R)
+
+
+def _dense_any_r(dtype, R, n, seed):
+    """R replicas whose elements sit at positions {0, 1, 2, 10, 20} x h on a
+    line (floats, h = 0.75 * abs_tol: one step apart equal, two apart not),
+    or take one of three values (integers): clusters, ties and non-transitive
+    chains at most elements."""
+    rng = np.random.default_rng(seed)
+    t = oracle.NP_OF[dtype]
+    if dtype in ("f32", "f64"):
+        abs_tol = 1e-3
+        base = (rng.integers(-50, 50, size=n) * 100).astype(t) * t(abs_tol)
+        steps = np.array([0, 1, 2, 10, 20], dtype=t)
+        reps = [base + steps[rng.integers(0, 5, size=n)] * t(0.75 * abs_tol) for _ in range(R)]
+        return [np.ascontiguousarray(x, dtype=t) for x in reps], (abs_tol, 0.0)
+    info = np.iinfo(t)
+    alphabet = np.stack([rng.integers(info.min, info.max, size=n, dtype=t, endpoint=True) for _ in range(3)])
+    return [np.ascontiguousarray(alphabet[rng.integers(0, 3, size=n), np.arange(n)]) for _ in range(R)], (0.0, 0.0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "i32", "u8"])
+@pytest.mark.parametrize("R", [2, 4, 5, 8])
+def test_dense_disagreement_other_r(dtype, R):
+    """As above for R = 2 (replica 0 always wins) and R >= 4 (the float form
+    that re-votes a flagged sub-batch, the bits-first form of the others)."""
+    for k, n in enumerate((9, 4096 + 100, 100_003)):
+        reps, tol = _dense_any_r(dtype, R, n, seed=900 + 10 * R + k)
+        ref = oracle.vote(reps, dtype, *tol)
+        if n > 1000:
+            assert ref["no_majority"] > 0 and max(ref["mismatch"]) > 0
+        assert_same(gpu_vote(reps, dtype, *tol), ref, R)
