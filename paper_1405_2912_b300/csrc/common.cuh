@@ -499,22 +499,24 @@ __device__ __forceinline__ void store_elem(uint8_t *p, typename Elem<K>::V v)
     else *p = (uint8_t)v;
 }
 
-// 16-byte vectors per lane that a sub-batch loads from each replica.  (4 for
+// 16-byte vectors per lane that a sub-batch loads from each replica.  (8 for
+// R = 2 measured 1-2 % slower than 4 on every kind with 256 MB replicas; 4 for
 // R = 5..6 of the kinds with the equal-bits fast path measured the same as 2
 // on the 5 x 64M f64 / i32 workloads and spilled.)
 template <int K, int R>
-constexpr int kSubBatch = (K == K_B1 && R <= 2) ? 4 : ((R <= 2) ? 8 : (R <= 4 ? 4 : 2));
+constexpr int kSubBatch = (R <= 4) ? 4 : 2;
 
 // Launch shape of the voter kernels for one (kind, R), chosen by measurement
-// on B300 (3 x 256M f32; 5 x 64M f64 and i32): warps per CTA (one CTA per SM)
-// and whether a warp prefetches its next block into L2 while voting the
-// current one.  The f32 R <= 3 vote is ALU-heavier per byte and gains from the
-// prefetch with 12 warps (6.7 TB/s against 6.2 with 16); the kinds with the
-// equal-bits fast path run best with 16 warps and no prefetch, whose extra L2
-// footprint costs more than it hides there.
+// on B300 (3 x 256M f32; 5 x 64M f64 and i32; 256 MB replicas of every kind
+// for R = 2): warps per CTA (one CTA per SM) and whether a warp prefetches its
+// next block into L2 while voting the current one.  The f32 R = 3 closed form
+// is ALU-heavier per byte and gains from the prefetch with 12 warps (6.7 TB/s
+// against 6.2 with 16); every other (kind, R) runs best with 16 warps and no
+// prefetch, whose extra L2 footprint costs more than it hides there (f32 R = 2:
+// 5.95 against 5.68 TB/s).
 template <int K, int R>
 struct VotePolicy {
-    static constexpr bool kPrefetch = (K == K_F32 && R <= 3);
+    static constexpr bool kPrefetch = (K == K_F32 && R == 3);
     static constexpr int kWarps = kPrefetch ? 12 : 16;
 };
 
