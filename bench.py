@@ -108,6 +108,23 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def warm_up(steps, step, stream, min_seconds=0.2):
+    """At least `steps` untimed steps, run right before the timed region and
+    continued until `min_seconds` of wall time have passed (synchronising every
+    16 steps), so that the GPU has left its idle clocks when timing starts.
+    Without it, a short timed region after an idle pause (the clock sampler's
+    start-up) ran ~16 ms slower in total."""
+    t0 = time.perf_counter()
+    k = 0
+    while k < steps or time.perf_counter() - t0 < min_seconds:
+        step()
+        k += 1
+        if k % 16 == 0:
+            stream.synchronize()
+    stream.synchronize()
+    return k
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -265,13 +282,10 @@ def run_ours(args, problem, ws, rank, local):
     pd = ctypes.byref(desc)
     torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        fv.check(fv.ft_vote(pd, sh), "ft_vote")
-    torch.cuda.synchronize()
-
     ev_start, ev_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     sampler.start()
+    warm_steps = warm_up(args.warmup, lambda: fv.check(fv.ft_vote(pd, sh), "ft_vote"), stream)
     launches0 = fv.ft_launch_count()
     barrier(ws)
     torch.cuda.synchronize()
@@ -352,7 +366,8 @@ def run_ours(args, problem, ws, rank, local):
                "sample": f"first {n_s} of {n} elements, 4 KiB-aligned chunks on {cores} threads, one pass"}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4),
+        "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
+        "ms_per_step": round(1e3 * t_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": problem.dtype,
         "data": "synthetic",
         "config": config_of(problem, ws, args.workload),
@@ -527,9 +542,8 @@ def run_size_sweep(args, dev):
         d = fv.make_desc(reps, out, crc, st, p.abs_tol, p.rel_tol)
         pd = ctypes.byref(d)
         sh = fv.stream_handle()
-        for _ in range(3):
-            fv.ft_vote(pd, sh)
-        torch.cuda.synchronize()
+        # the oracle runs between sizes leave the GPU idle: warm it up again
+        warm_up(3, lambda: fv.ft_vote(pd, sh), torch.cuda.current_stream())
         ts = []
         for _ in range(21):
             t0 = time.perf_counter()

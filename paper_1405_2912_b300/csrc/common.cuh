@@ -62,6 +62,7 @@ struct CrcTables {
     uint32_t comb[8][16][32];   // comb[p][v][l] = (v << 4p) * x^(8*128*(31-l))
     uint32_t shift4096[8][16];  // shift4096[p][v] = (v << 4p) * x^(8*4096)
     uint32_t init4096;          // 0xFFFFFFFF * x^(8*4096): initial-value term of a full block
+    uint32_t shift_pow[32][8][16];   // shift_pow[j][p][v] = (v << 4p) * x^(8 * 2^j)
 };
 
 constexpr CrcTables make_crc_tables()
@@ -95,6 +96,14 @@ constexpr CrcTables make_crc_tables()
         for (int p = 0; p < 8; ++p)
             for (uint32_t v = 0; v < 16; ++v) t.shift4096[p][v] = gf_mul(v << (4 * p), K);
         t.init4096 = gf_mul(0xFFFFFFFFu, K);
+    }
+    {
+        uint32_t K = gf_xpow8(1);                   // x^8, then squared: x^(8 * 2^j)
+        for (int j = 0; j < 32; ++j) {
+            for (int p = 0; p < 8; ++p)
+                for (uint32_t v = 0; v < 16; ++v) t.shift_pow[j][p][v] = gf_mul(v << (4 * p), K);
+            K = gf_mul(K, K);
+        }
     }
     return t;
 }
@@ -223,17 +232,37 @@ __device__ __forceinline__ uint32_t tile_crc_full(const uint4 *tile, const uint3
     return warp_xor(r);
 }
 
-// Raw register of the first `len` (< 4096, any) bytes of the tile; slow path
-// for a partial last block.
-static __device__ __noinline__ uint32_t tile_crc_partial(const uint4 *tile, const uint32_t *s_crc, uint32_t len, int lane)
+// c * x^(8k) mod P: the register after k more zero bytes (k < 2^32), one
+// nibble-table multiplication by x^(8 * 2^j) per set bit j of k.
+__device__ __forceinline__ uint32_t shift_bytes(uint32_t c, uint32_t k)
+{
+    for (int j = 0; k != 0u; ++j, k >>= 1) {
+        if (!(k & 1u)) continue;
+        uint32_t r = 0;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) r ^= g_crc.shift_pow[j][p][(c >> (4 * p)) & 15u];
+        c = r;
+    }
+    return c;
+}
+
+// Raw register of the first `len` (< 4096, any) bytes of the tile (a partial
+// last block): lane l digests its bytes [128 l, 128 l + 128) that lie below
+// len, four at a time and the rest one by one, and shifts its register over
+// the bytes that follow them.
+static __device__ __noinline__ uint32_t tile_crc_partial(const uint4 *tile, const uint32_t *s_crc, const CrcLane &L,
+                                                         uint32_t len, int lane)
 {
     const uint32_t start = 128u * lane;
     const uint32_t seg = len > start ? min(128u, len - start) : 0u;
     const uint8_t *bytes = reinterpret_cast<const uint8_t *>(tile) + 144u * lane;
+    const uint32_t *words = reinterpret_cast<const uint32_t *>(bytes);
     uint32_t c = 0;
-    for (uint32_t k = 0; k < seg; ++k) c = crc_step1(s_crc, c, bytes[k]);
+    uint32_t k = 0;
+    for (; k + 4 <= seg; k += 4) c = crc_step4(s_crc, L, c ^ words[k >> 2]);
+    for (; k < seg; ++k) c = crc_step1(s_crc, c, bytes[k]);
     const uint32_t after = len > start + 128u ? len - start - 128u : 0u;
-    c = gf_mul(c, gf_xpow8(after));
+    c = shift_bytes(c, after);
     return warp_xor(c);
 }
 
@@ -821,36 +850,48 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     __syncwarp();
 }
 
-// The partial last block (a.tail_bytes bytes), element by element.
+// The partial last block (a.tail_bytes bytes), element by element.  Lane l
+// takes the elements of bytes [128 l, 128 l + 128).  The loads of a chunk of
+// C elements are issued together before any of its stores: the compiler
+// cannot move a load above a store to the output, which may alias for all
+// it knows, so one element at a time would pay one memory latency each.
 template <int K, int R>
 __device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long long b, uint4 *tile,
-                                             const uint32_t *s_crc, LaneStats<R> &st, int lane)
+                                             const uint32_t *s_crc, const CrcLane &L, LaneStats<R> &st, int lane)
 {
     using E = Elem<K>;
     using V = typename E::V;
     constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
+    constexpr int C = (R <= 4) ? 8 : 4;
     const typename E::Ctx c = E::ctx(a.abs_tol, a.rel_tol);
     const uint32_t len = a.tail_bytes;
     const unsigned long long boff = b * kBlockBytes;
     const uint32_t e0 = (128u * lane) / E::kSize;
     const uint32_t e1 = min(128u * (lane + 1), len) / E::kSize;
     uint8_t *tb = reinterpret_cast<uint8_t *>(tile);
-    for (uint32_t e = e0; e < e1; ++e) {
-        const unsigned long long off = boff + (unsigned long long)e * E::kSize;
-        V x[R];
+    for (uint32_t e = e0; e < e1; e += C) {
+        V x[C][R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[r] = load_elem<K>(a.rep[r] + off);
-        V y;
-        uint32_t m;
-        vote_elem<K, R>(x, c, y, m);
-        store_elem<K>(a.out + off, y);
-        const uint32_t bo = e * E::kSize;
-        store_elem<K>(tb + tile_index(bo >> 4) * 16 + (bo & 15u), y);
-        if (m) st.add_one(m, b * kEpb + e);
+        for (int j = 0; j < C; ++j)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                x[j][r] = (e + j < e1) ? load_elem<K>(a.rep[r] + boff + (unsigned long long)(e + j) * E::kSize)
+                                       : V(0);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            if (e + j >= e1) break;
+            V y;
+            uint32_t m;
+            vote_elem<K, R>(x[j], c, y, m);
+            store_elem<K>(a.out + boff + (unsigned long long)(e + j) * E::kSize, y);
+            const uint32_t bo = (e + j) * E::kSize;
+            store_elem<K>(tb + tile_index(bo >> 4) * 16 + (bo & 15u), y);
+            if (m) st.add_one(m, b * kEpb + e + j);
+        }
     }
     __syncwarp();
-    const uint32_t raw = tile_crc_partial(tile, s_crc, len, lane);
-    if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ gf_mul(0xFFFFFFFFu, gf_xpow8(len)));
+    const uint32_t raw = tile_crc_partial(tile, s_crc, L, len, lane);
+    if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ shift_bytes(0xFFFFFFFFu, len));
     __syncwarp();
 }
 

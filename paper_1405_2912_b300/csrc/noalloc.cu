@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(W * 32, 1) noalloc_batched_kernel(const Noallo
         if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
-            vote_tail_block<K, R>(a, a.nfull, tile, s_crc, ts, lane);
+            vote_tail_block<K, R>(a, a.nfull, tile, s_crc, L, ts, lane);
             st.merge(ts);
         }
     }

@@ -137,9 +137,10 @@ __global__ void reset_stats_kernel(ft_stats *s) { reset_stats(s, threadIdx.x); }
 
 // ---------------------------------------------------------------------------
 // K1: persistent single-task voter.  Warps take 4 KiB blocks in grid-stride
-// order; consecutive warps of a CTA take consecutive blocks.
+// order; consecutive warps of a CTA take consecutive blocks.  PF: each warp
+// prefetches its next block into L2.
 // ---------------------------------------------------------------------------
-template <int K, int R, int W>
+template <int K, int R, int W, bool PF>
 __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -157,23 +158,22 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
     const unsigned long long step = (unsigned long long)gridDim.x * W;
     const unsigned long long gw = (unsigned long long)blockIdx.x * W + w;
     for (unsigned long long b = gw; b < a.nfull; b += step)
-        vote_full_block<K, R>(a, b, VotePolicy<K, R>::kPrefetch ? b + step : ~0ull, tile, s_crc, s_comb, L, st,
+        vote_full_block<K, R>(a, b, PF ? b + step : ~0ull, tile, s_crc, s_comb, L, st,
                               lane);
     if (a.tail_bytes && a.nfull % step == gw) {
         // the partial last block goes to the warp whose turn it would be
         LaneStats<R> ts;
         ts.init();
-        vote_tail_block<K, R>(a, a.nfull, tile, s_crc, ts, lane);
+        vote_tail_block<K, R>(a, a.nfull, tile, s_crc, L, ts, lane);
         st.merge(ts);
     }
     st.flush(a.stats, lane);
 }
 
-template <int K, int R>
-static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
+template <int K, int R, int kVoteWarps, bool PF>
+static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
 {
-    constexpr int kVoteWarps = VotePolicy<K, R>::kWarps;
-    auto fn = vote_kernel<K, R, kVoteWarps>;
+    auto fn = vote_kernel<K, R, kVoteWarps, PF>;
     const size_t smem = Smem::bytes(kVoteWarps);
     int sms = 0, per_sm = 0;
     int rc = occupancy(reinterpret_cast<const void *>(fn), kVoteWarps * 32, smem, &sms, &per_sm);
@@ -186,6 +186,24 @@ static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *c
     if (grid < 1) grid = 1;
     fn<<<(unsigned)grid, kVoteWarps * 32, smem, s>>>(a);
     return check_launch(1);
+}
+
+// Votes of up to 32768 blocks (128 MiB of output) have at most a few blocks
+// per warp, so latency, not bandwidth, sets their time: for them the shape
+// with more warps and no prefetch measured faster even where the policy
+// prefers the prefetching one (f32 R = 3: 3 x 16M 52 against 58 us, 3 x 4M 18
+// against 20 us; equal at 3 x 64M; 6.7 against 6.25 TB/s the other way at
+// 3 x 256M).
+constexpr unsigned long long kSmallVoteBlocks = 32768;
+
+template <int K, int R>
+static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
+{
+    using P = VotePolicy<K, R>;
+    if constexpr (P::kPrefetch) {
+        if (a.nfull + (a.tail_bytes ? 1 : 0) <= kSmallVoteBlocks) return launch_vote_shape<K, R, 16, false>(a, s, cfg);
+    }
+    return launch_vote_shape<K, R, P::kWarps, P::kPrefetch>(a, s, cfg);
 }
 
 template <int K>
@@ -290,10 +308,10 @@ __global__ void __launch_bounds__(W * 32, 1)
             uint8_t *tb = reinterpret_cast<uint8_t *>(tile);
             for (uint32_t i = nvec * 16 + lane; i < rem; i += 32) tb[tile_index(i >> 4) * 16 + (i & 15u)] = src[i];
             __syncwarp();
-            acc = gf_mul(acc, gf_xpow8(rem)) ^ tile_crc_partial(tile, s_crc, rem, lane);
+            acc = shift_bytes(acc, rem) ^ tile_crc_partial(tile, s_crc, L, rem, lane);
             __syncwarp();
         }
-        const uint32_t init = (len == block_bytes) ? init_full : gf_mul(0xFFFFFFFFu, gf_xpow8(len));
+        const uint32_t init = (len == block_bytes) ? init_full : shift_bytes(0xFFFFFFFFu, (uint32_t)len);
         if (lane == 0) out[b] = ~(acc ^ init);
     }
 }
