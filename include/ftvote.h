@@ -234,6 +234,30 @@ int ft_submit(ft_server *srv, const ft_vote_desc *desc, uint64_t *ticket);
  * stays in flight; poll again).  FT_ENOTFOUND: unknown ticket. */
 int ft_poll(ft_server *srv, uint64_t ticket, int64_t timeout_us, ft_result *res);
 
+/* Bulk forms for clients with many requests in flight: one call and one
+ * acquisition of the server's lock for a run of requests.
+ *
+ * ft_submit_many submits descs[0..n) in order, each as ft_submit would, and
+ * stops at the first request that does not fit the free budget or the
+ * in-flight limit right now.  descs is a host array of n pointers; tickets
+ * (n entries) receives the ticket of each accepted request, and *accepted
+ * their number, a prefix of the array (0..n).  Returns FT_OK (the requests
+ * after the accepted prefix were refused for now: retry them later), or
+ * FT_EINVAL when the first request not accepted is invalid (*accepted is its
+ * index) or for bad arguments.
+ *
+ * ft_poll_many waits up to timeout_us (as ft_poll) for tickets[0], then
+ * retires the longest prefix of tickets[0..n) whose requests are done,
+ * filling results[i] (n entries, or NULL) for each, and sets *ndone to its
+ * length.  Returns FT_OK (including *ndone == 0 after a wait of 0), or
+ * FT_ETIMEDOUT when tickets[0] is not done, or FT_ENOTFOUND when a ticket of
+ * the prefix is unknown (*ndone counts the requests retired before it), or
+ * FT_EINVAL. */
+int ft_submit_many(ft_server *srv, const ft_vote_desc *const *descs, int32_t n, uint64_t *tickets,
+                   int32_t *accepted);
+int ft_poll_many(ft_server *srv, const uint64_t *tickets, int32_t n, int64_t timeout_us, ft_result *results,
+                 int32_t *ndone);
+
 /* Hold back (paused != 0) or release the launching of admitted requests.
  * While paused, requests are admitted and queued on the host but no batch
  * starts, so ft_poll on them times out: the host-side way to exercise the

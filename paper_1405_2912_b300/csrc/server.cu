@@ -320,56 +320,67 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     return FT_OK;
 }
 
-int ft_submit(ft_server *s, const ft_vote_desc *desc, uint64_t *ticket)
+}  // extern "C"
+
+namespace {
+
+// Validates one request and fills everything but its ticket (no lock held).
+int prepare_request(const ft_server *s, const ft_vote_desc *desc, Request &r)
 {
-    if (!s || !desc || !ticket) return FT_EINVAL;
+    if (!desc) return FT_EINVAL;
     // the server supplies the statistics buffer when the caller gives none
     ft_vote_desc d = *desc;
     ft_stats dummy;
     const bool user = d.stats != nullptr;
     if (!user) d.stats = &dummy;
-    int rc = ftv::validate_desc(&d);
+    const int rc = ftv::validate_desc(&d);
     if (rc != FT_OK) return rc;
     const unsigned long long bytes = (unsigned long long)(d.R + 1) * d.n * ftv::dtype_size(d.dtype);
     if (bytes > s->cfg.mem_budget_bytes) return FT_EINVAL;   // can never be admitted
-    Request r;
     r.args = ftv::make_task_args(&d);
     r.user_stats = user ? desc->stats : nullptr;
     r.bytes = bytes;
     r.submit_us = now_us();
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) return FT_EINVAL;
-    if (s->inflight_bytes + bytes > s->cfg.mem_budget_bytes || s->inflight >= s->cfg.max_inflight) return FT_EAGAIN;
-    const unsigned long long t = s->next_ticket++;
-    s->reqs.emplace(t, r);
-    s->pending.push_back(t);
-    s->inflight_bytes += bytes;
-    s->inflight += 1;
-    *ticket = t;
-    s->cv_work.notify_one();
     return FT_OK;
 }
 
-int ft_poll(ft_server *s, uint64_t ticket, int64_t timeout_us, ft_result *res)
+// Admits a prepared request (lock held): FT_OK with its ticket, or FT_EAGAIN.
+int admit_locked(ft_server *s, const Request &r, uint64_t *ticket)
 {
-    if (!s) return FT_EINVAL;
-    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->inflight_bytes + r.bytes > s->cfg.mem_budget_bytes || s->inflight >= s->cfg.max_inflight) return FT_EAGAIN;
+    const unsigned long long t = s->next_ticket++;
+    s->reqs.emplace(t, r);
+    s->pending.push_back(t);
+    s->inflight_bytes += r.bytes;
+    s->inflight += 1;
+    *ticket = t;
+    return FT_OK;
+}
+
+// Waits (lock held) up to timeout_us (< 0: no limit, 0: not at all) for a
+// ticket: FT_OK when it is done, FT_ETIMEDOUT, or FT_ENOTFOUND.
+int wait_done_locked(ft_server *s, std::unique_lock<std::mutex> &lk, uint64_t ticket, int64_t timeout_us)
+{
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return FT_ENOTFOUND;
-    if (!it->second.done) {
-        auto ready = [&] {
-            auto j = s->reqs.find(ticket);
-            return j == s->reqs.end() || j->second.done;
-        };
-        if (timeout_us < 0) {
-            s->cv_done.wait(lk, ready);
-        } else if (timeout_us > 0) {
-            s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
-        }
-        it = s->reqs.find(ticket);
-        if (it == s->reqs.end()) return FT_ENOTFOUND;
-        if (!it->second.done) return FT_ETIMEDOUT;
+    if (it->second.done) return FT_OK;
+    auto ready = [&] {
+        auto j = s->reqs.find(ticket);
+        return j == s->reqs.end() || j->second.done;
+    };
+    if (timeout_us < 0) {
+        s->cv_done.wait(lk, ready);
+    } else if (timeout_us > 0) {
+        s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
     }
+    it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return FT_ENOTFOUND;
+    return it->second.done ? FT_OK : FT_ETIMEDOUT;
+}
+
+// Retires a done request (lock held), filling *res when it is not NULL.
+void retire_locked(ft_server *s, std::unordered_map<unsigned long long, Request>::iterator it, ft_result *res)
+{
     Request &r = it->second;
     if (res) {
         res->status = r.status;
@@ -382,7 +393,75 @@ int ft_poll(ft_server *s, uint64_t ticket, int64_t timeout_us, ft_result *res)
     s->inflight_bytes -= r.bytes;
     s->inflight -= 1;
     s->reqs.erase(it);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ft_submit(ft_server *s, const ft_vote_desc *desc, uint64_t *ticket)
+{
+    if (!s || !desc || !ticket) return FT_EINVAL;
+    Request r;
+    int rc = prepare_request(s, desc, r);
+    if (rc != FT_OK) return rc;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return FT_EINVAL;
+    if ((rc = admit_locked(s, r, ticket)) == FT_OK) s->cv_work.notify_one();
+    return rc;
+}
+
+int ft_submit_many(ft_server *s, const ft_vote_desc *const *descs, int32_t n, uint64_t *tickets, int32_t *accepted)
+{
+    if (!s || !accepted || n < 0 || (n > 0 && (!descs || !tickets))) return FT_EINVAL;
+    *accepted = 0;
+    std::vector<Request> rs(n);
+    int valid = 0, rc_bad = FT_OK;
+    for (; valid < n; ++valid)
+        if ((rc_bad = prepare_request(s, descs[valid], rs[valid])) != FT_OK) break;
+    int k = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return FT_EINVAL;
+        for (; k < valid; ++k)
+            if (admit_locked(s, rs[k], &tickets[k]) != FT_OK) break;
+        if (k > 0) s->cv_work.notify_one();
+    }
+    *accepted = k;
+    return (k == valid && valid < n) ? rc_bad : FT_OK;
+}
+
+int ft_poll(ft_server *s, uint64_t ticket, int64_t timeout_us, ft_result *res)
+{
+    if (!s) return FT_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const int rc = wait_done_locked(s, lk, ticket, timeout_us);
+    if (rc != FT_OK) return rc;
+    retire_locked(s, s->reqs.find(ticket), res);
     return FT_OK;
+}
+
+int ft_poll_many(ft_server *s, const uint64_t *tickets, int32_t n, int64_t timeout_us, ft_result *results,
+                 int32_t *ndone)
+{
+    if (!s || !ndone || n < 0 || (n > 0 && !tickets)) return FT_EINVAL;
+    *ndone = 0;
+    if (n == 0) return FT_OK;
+    std::unique_lock<std::mutex> lk(s->mu);
+    int rc = wait_done_locked(s, lk, tickets[0], timeout_us);
+    if (rc != FT_OK) return rc;
+    int k = 0;
+    for (; k < n; ++k) {
+        auto it = s->reqs.find(tickets[k]);
+        if (it == s->reqs.end()) {
+            rc = FT_ENOTFOUND;
+            break;
+        }
+        if (!it->second.done) break;
+        retire_locked(s, it, results ? &results[k] : nullptr);
+    }
+    *ndone = k;
+    return rc;
 }
 
 int ft_server_pause(ft_server *s, int32_t paused)

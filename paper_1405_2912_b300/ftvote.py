@@ -113,6 +113,11 @@ ft_plan_destroy = _sig("ft_plan_destroy", ctypes.c_int, _P)
 ft_server_create = _sig("ft_server_create", ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(ft_server_config))
 ft_submit = _sig("ft_submit", ctypes.c_int, _P, ctypes.POINTER(ft_vote_desc), ctypes.POINTER(ctypes.c_uint64))
 ft_poll = _sig("ft_poll", ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ft_result))
+# bulk forms: arrays are passed by address (int) so that callers can pass
+# offsets into one long array without building new ctypes objects
+ft_submit_many = _sig("ft_submit_many", ctypes.c_int, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32))
+ft_poll_many = _sig("ft_poll_many", ctypes.c_int, _P, _P, ctypes.c_int32, ctypes.c_int64, _P,
+                    ctypes.POINTER(ctypes.c_int32))
 ft_server_destroy = _sig("ft_server_destroy", ctypes.c_int, _P)
 ft_server_pause = _sig("ft_server_pause", ctypes.c_int, _P, ctypes.c_int32)
 ft_clock_us = _sig("ft_clock_us", ctypes.c_double)

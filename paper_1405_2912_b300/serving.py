@@ -5,12 +5,16 @@ scheduled arrival time (host monotonic clock of the library, ft_clock_us),
 retries requests that the budget refuses, collects results in arrival order,
 and reports latency = completion time (the batch's completion callback) minus
 the scheduled arrival time, so that queueing behind the budget and in the
-server both count.  It only calls the C ABI; all voting runs on the GPU.
+server both count.  Each pass of its loop submits every request that has
+arrived with one ft_submit_many and retires the finished ones with one
+ft_poll_many, so the generator's own cost does not grow with the request
+rate.  It only calls the C ABI; all voting runs on the GPU.
 """
 from __future__ import annotations
 
 import collections
 import ctypes
+import gc
 
 import numpy as np
 
@@ -22,45 +26,52 @@ def replay(srv, descs, arrivals_s, payload_of, start_delay_us=2000.0):
 
     Returns a dict with per-request latencies (us), the number of budget
     refusals, and the wall span from the first arrival to the last completion.
+    Python's cyclic garbage collector is paused for the replay: one of its
+    full collections stalls the submitting loop for milliseconds, which would
+    show as server latency.
     """
+    was_enabled = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        return _replay(srv, descs, arrivals_s, payload_of, start_delay_us)
+    finally:
+        if was_enabled:
+            gc.enable()
+
+
+def _replay(srv, descs, arrivals_s, payload_of, start_delay_us):
     n = len(arrivals_s)
-    t0 = fv.ft_clock_us() + start_delay_us
+    m = max(n, 1)
+    # one descriptor pointer, ticket and result slot per request, laid out
+    # before the clock starts; the loop passes offsets into them
+    dptr = (ctypes.c_void_p * m)(*[ctypes.addressof(descs[k]) for k in payload_of])
+    tickets = (ctypes.c_uint64 * m)()
+    results = (fv.ft_result * m)()
+    a_d, a_t, a_r = ctypes.addressof(dptr), ctypes.addressof(tickets), ctypes.addressof(results)
+    rsz = ctypes.sizeof(fv.ft_result)
+    acc, nd = ctypes.c_int32(), ctypes.c_int32()
+    pacc, pnd = ctypes.byref(acc), ctypes.byref(nd)
+    submit_many, poll_many, clock = fv.ft_submit_many, fv.ft_poll_many, fv.ft_clock_us
+    t0 = clock() + start_delay_us
     arr = t0 + np.asarray(arrivals_s, dtype=np.float64) * 1e6
-    lat = np.zeros(n)
-    done_at = np.zeros(n)
-    outstanding = collections.deque()
-    res = fv.ft_result()
-    tk = ctypes.c_uint64()
-    i = 0
+    i = head = 0
     refused = 0
-    submit = fv.ft_submit
-    poll = fv.ft_poll
-    clock = fv.ft_clock_us
-    pres = ctypes.byref(res)
-    ptk = ctypes.byref(tk)
-    dptr = [ctypes.byref(d) for d in descs]
-    errors = 0
-    while i < n or outstanding:
-        now = clock()
-        while i < n and arr[i] <= now:
-            rc = submit(srv, dptr[payload_of[i]], ptk)
-            if rc == fv.FT_EAGAIN:
-                refused += 1
-                break
-            fv.check(rc, "ft_submit")
-            outstanding.append((tk.value, i))
-            i += 1
-        while outstanding:
-            t, k = outstanding[0]
-            rc = poll(srv, t, 0, pres)
-            if rc == fv.FT_ETIMEDOUT:
-                break
-            fv.check(rc, "ft_poll")
-            if res.status != fv.FT_OK:
-                errors += 1
-            lat[k] = res.done_us - arr[k]
-            done_at[k] = res.done_us
-            outstanding.popleft()
+    while head < n:
+        due = int(np.searchsorted(arr, clock(), side="right"))   # arrivals that have passed
+        if due > i:
+            fv.check(submit_many(srv, a_d + 8 * i, due - i, a_t + 8 * i, pacc), "ft_submit_many")
+            if acc.value < due - i:
+                refused += 1              # the budget is full: retry on the next pass
+            i += acc.value
+        if head < i:
+            rc = poll_many(srv, a_t + 8 * head, i - head, 0, a_r + rsz * head, pnd)
+            if rc != fv.FT_ETIMEDOUT:
+                fv.check(rc, "ft_poll_many")
+            head += nd.value
+    done_at = np.array([results[k].done_us for k in range(n)], dtype=np.float64)
+    errors = sum(1 for k in range(n) if results[k].status != fv.FT_OK)
+    lat = done_at - arr
     span_s = (done_at.max() - arr.min()) / 1e6 if n else 0.0
     return {"latency_us": lat, "refused": refused, "span_s": span_s, "errors": errors}
 
@@ -72,6 +83,7 @@ def summarize(r, bytes_per_req):
             "p50_us": round(float(np.percentile(lat, 50)), 1) if n else None,
             "p99_us": round(float(np.percentile(lat, 99)), 1) if n else None,
             "mean_us": round(float(lat.mean()), 1) if n else None,
+            "max_us": round(float(lat.max()), 1) if n else None,
             "req_per_s": round(n / r["span_s"], 1) if r["span_s"] > 0 else None,
             "gb_per_s": round(float(np.sum(bytes_per_req)) / r["span_s"] / 1e9, 2) if r["span_s"] > 0 else None,
             "budget_refusals": int(r["refused"]), "errors": int(r["errors"])}

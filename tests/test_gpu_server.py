@@ -255,3 +255,70 @@ def test_concurrent_clients():
     finally:
         fv.ft_server_destroy(srv)
     assert not errors, errors[:3]
+
+
+def test_bulk_submit_and_poll():
+    """ft_submit_many admits the prefix that fits the budget and stops at an
+    invalid request; ft_poll_many retires the finished prefix of a ticket
+    run; results are those of single votes."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    probs = _requests(k=6, seed=11)
+    tasks = [DevTask(p) for p in probs]
+    need = [(p.R + 1) * p.n * p.itemsize for p in probs]
+    assert need[4] + need[5] <= sum(need[:4])       # the last two fit once the first four are retired
+    ptrs = (ctypes.c_void_p * 6)(*[ctypes.addressof(t.desc) for t in tasks])
+    tickets = (ctypes.c_uint64 * 6)()
+    results = (fv.ft_result * 6)()
+    acc, nd = ctypes.c_int32(), ctypes.c_int32()
+    A = ctypes.addressof
+    srv = _server(budget=sum(need[:4]))
+    try:
+        fv.ft_server_pause(srv, 1)
+        # the first four fit, the fifth is refused for now
+        assert fv.ft_submit_many(srv, A(ptrs), 6, A(tickets), ctypes.byref(acc)) == fv.FT_OK
+        assert acc.value == 4
+        assert len({tickets[k] for k in range(4)}) == 4
+        # nothing has run: the first ticket times out, nothing is retired
+        assert fv.ft_poll_many(srv, A(tickets), 4, 0, A(results), ctypes.byref(nd)) == fv.FT_ETIMEDOUT
+        assert nd.value == 0
+        fv.ft_server_pause(srv, 0)
+        head = 0
+        deadline = time.time() + 30
+        while head < 4 and time.time() < deadline:
+            rc = fv.ft_poll_many(srv, A(tickets) + 8 * head, 4 - head, 1_000_000,
+                                 A(results) + ctypes.sizeof(fv.ft_result) * head, ctypes.byref(nd))
+            assert rc in (fv.FT_OK, fv.FT_ETIMEDOUT)
+            head += nd.value
+        assert head == 4
+        # retired tickets are unknown now; the count stops before them
+        assert fv.ft_poll_many(srv, A(tickets), 2, 0, None, ctypes.byref(nd)) == fv.FT_ENOTFOUND
+        assert nd.value == 0
+        # the rest fit now; an invalid request stops the run at its index
+        bad = fv.ft_vote_desc.from_buffer_copy(tasks[0].desc)
+        bad.R = 1
+        ptrs2 = (ctypes.c_void_p * 3)(A(tasks[4].desc), A(bad), A(tasks[5].desc))
+        tk2 = (ctypes.c_uint64 * 3)()
+        assert fv.ft_submit_many(srv, A(ptrs2), 3, A(tk2), ctypes.byref(acc)) == fv.FT_EINVAL
+        assert acc.value == 1
+        tickets[4] = tk2[0]
+        ptrs3 = (ctypes.c_void_p * 1)(A(tasks[5].desc))
+        assert fv.ft_submit_many(srv, A(ptrs3), 1, A(tickets) + 8 * 5, ctypes.byref(acc)) == fv.FT_OK
+        assert acc.value == 1
+        for k in (4, 5):
+            assert fv.ft_poll_many(srv, A(tickets) + 8 * k, 1, -1, A(results) + ctypes.sizeof(fv.ft_result) * k,
+                                   ctypes.byref(nd)) == fv.FT_OK and nd.value == 1
+        # a run of zero is accepted and does nothing
+        assert fv.ft_submit_many(srv, A(ptrs), 0, A(tickets), ctypes.byref(acc)) == fv.FT_OK and acc.value == 0
+        assert fv.ft_poll_many(srv, A(tickets), 0, 0, None, ctypes.byref(nd)) == fv.FT_OK and nd.value == 0
+    finally:
+        fv.ft_server_destroy(srv)
+    torch.cuda.synchronize()
+    for k, (p, t) in enumerate(zip(probs, tasks)):
+        assert results[k].status == fv.FT_OK and results[k].done_us >= results[k].submit_us
+        got = t.result()
+        ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        assert_same(got, ref, p.R)
+        sd = _stats_dict(results[k].stats, p.R)
+        for key, v in sd.items():
+            assert np.array_equal(np.asarray(got[key]), np.asarray(v)), (k, key)
