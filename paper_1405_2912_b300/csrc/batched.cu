@@ -31,12 +31,9 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *s_comb = s_crc + kCrcWords;
-    uint4 *tiles = reinterpret_cast<uint4 *>(s_comb + kCombWords);
-    load_crc_tables(s_crc, s_comb);
+    load_crc_tables<W>(s_crc);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint4 *tile = tiles + w * kTileVecs;
     CrcLane L;
     L.init(lane);
     LaneStats<R> st;
@@ -60,12 +57,12 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
         const unsigned long long b0 = k * (unsigned long long)g.tile_blocks;
         const unsigned long long b1 = min(b0 + (unsigned long long)g.tile_blocks, a.nfull);
         for (unsigned long long b = b0; b < b1; ++b)
-            vote_full_block<K, R>(a, b, (VotePolicy<K, R>::kPrefetch && b + 1 < b1) ? b + 1 : ~0ull, tile, s_crc,
-                                  s_comb, L, st, lane);
+            vote_full_block<K, R>(a, b, (VotePolicy<K, R>::kPrefetch && b + 1 < b1) ? b + 1 : ~0ull, s_crc, L,
+                                  st, lane);
         if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
-            vote_tail_block<K, R>(a, a.nfull, tile, s_crc, L, ts, lane);
+            vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
             st.merge(ts);
         }
     }
@@ -136,7 +133,7 @@ int group_occupancy(int kind, int R, int *sms, int *per_sm)
     const void *fn = group_kernel(kind, R);
     if (!fn) return FT_EINVAL;
     const int warps = group_warps(kind, R);
-    return occupancy(fn, warps * 32, Smem::bytes(warps), sms, per_sm);
+    return occupancy(fn, warps * 32, kSmemBytes, sms, per_sm);
 }
 
 int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
@@ -145,7 +142,7 @@ int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
     if (!fn) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
     const int warps = group_warps(g.kind, g.R);
-    const size_t smem = Smem::bytes(warps);
+    const size_t smem = kSmemBytes;
     int sms = 0, per_sm = 0;
     int rc = occupancy(fn, warps * 32, smem, &sms, &per_sm);
     if (rc != FT_OK) return rc;

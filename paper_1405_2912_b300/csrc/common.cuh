@@ -4,12 +4,14 @@
 // Work decomposition (shared by the single-task and the batched kernels): one
 // warp owns one 4096-byte block of the voted output at a time.  Lane l loads
 // the 16-byte vectors l, l+32, ..., l+224 of the block from every replica
-// (coalesced 128-bit loads), votes their elements in registers, stores the
-// voted vectors (coalesced 128-bit stores) and also writes them into a padded
-// per-warp shared-memory tile.  It then reads back the 128 contiguous bytes
-// [128 l, 128 l + 128) of the block from the tile and runs CRC32C over them;
-// the 32 lane CRCs are shifted to their place in the block by a per-lane
-// GF(2) multiplication and XOR-reduced across the warp.
+// (coalesced 128-bit loads), votes their elements in registers and stores the
+// voted vectors (coalesced 128-bit stores).  It digests the same eight
+// vectors in registers: its CRC32C register runs over them in order, and
+// folded into the tables of each vector's last step is the jump over the 496
+// bytes of other lanes' vectors up to its next one.  The 32 lane registers
+// are then moved to their place in the block by a per-lane GF(2)
+// multiplication and XOR-reduced across the warp.  Shared memory holds only
+// the lookup tables.
 #pragma once
 
 #include <cstdint>
@@ -59,7 +61,8 @@ __host__ __device__ constexpr uint32_t gf_xpow8(uint64_t nbytes)
 
 struct CrcTables {
     uint32_t slice[4][256];     // slicing-by-4 byte tables
-    uint32_t comb[8][16][32];   // comb[p][v][l] = (v << 4p) * x^(8*128*(31-l))
+    uint32_t slice_sh[4][256];  // slice[k][b] * x^(8*496): a step, then 496 zero bytes
+    uint32_t comb[8][16][32];   // comb[p][v][l] = (v << 4p) * x^(8*16*(31-l))
     uint32_t shift4096[8][16];  // shift4096[p][v] = (v << 4p) * x^(8*4096)
     uint32_t init4096;          // 0xFFFFFFFF * x^(8*4096): initial-value term of a full block
     uint32_t shift_pow[32][8][16];   // shift_pow[j][p][v] = (v << 4p) * x^(8 * 2^j)
@@ -78,8 +81,13 @@ constexpr CrcTables make_crc_tables()
             uint32_t prev = t.slice[k - 1][b];
             t.slice[k][b] = (prev >> 8) ^ t.slice[0][prev & 0xFFu];
         }
+    {
+        const uint32_t M = gf_xpow8(496);
+        for (int k = 0; k < 4; ++k)
+            for (uint32_t b = 0; b < 256; ++b) t.slice_sh[k][b] = gf_mul(t.slice[k][b], M);
+    }
     for (int l = 0; l < 32; ++l) {
-        uint32_t K = gf_xpow8(128ull * (31 - l));
+        uint32_t K = gf_xpow8(16ull * (31 - l));
         for (int p = 0; p < 8; ++p) {
             uint32_t bit[4] = {};
             for (int q = 0; q < 4; ++q) bit[q] = gf_mul(1u << (4 * p + q), K);
@@ -113,48 +121,69 @@ constexpr CrcTables kCrcHost = make_crc_tables();
 __device__ const CrcTables g_crc = kCrcHost;
 
 constexpr int kBlockBytes = 4096;
-constexpr int kTileVecs = 288;      // 256 vectors + one 16-byte pad per 128 bytes
 constexpr int kCombWords = 8 * 16 * 32;
 constexpr int kCrcRowWords = 64;    // one 256-byte row per byte value: 4 tables x 16 copies
 constexpr int kCrcWords = 256 * kCrcRowWords;
+// Shared-memory table image: slicing tables, shifted slicing tables, combine
+// tables, in that order (word offsets).
+constexpr int kCrcShOffset = kCrcWords;
+constexpr int kCombOffset = 2 * kCrcWords;
+constexpr int kTableWords = 2 * kCrcWords + kCombWords;
 constexpr uint64_t kNone = ~0ull;   // "no index yet"; reads as -1 through int64
 
 // The shared-memory image of the tables, built at compile time: the slicing
-// tables (row e holds T_k[e] for k = 0..3, 16 copies each) followed by the
-// per-lane combine tables.  A CTA copies it with 16-byte loads.
+// tables (row e holds T_k[e] for k = 0..3, 16 copies each), the shifted
+// slicing tables in the same layout, then the per-lane combine tables.  A CTA
+// copies it with 16-byte loads.
 struct alignas(16) CrcImage {
-    uint32_t w[kCrcWords + kCombWords];
+    uint32_t w[kTableWords];
 };
 
 constexpr CrcImage make_crc_image()
 {
     CrcImage im{};
-    for (int i = 0; i < kCrcWords; ++i) im.w[i] = kCrcHost.slice[(i >> 4) & 3][i >> 6];
+    for (int i = 0; i < kCrcWords; ++i) {
+        im.w[i] = kCrcHost.slice[(i >> 4) & 3][i >> 6];
+        im.w[kCrcShOffset + i] = kCrcHost.slice_sh[(i >> 4) & 3][i >> 6];
+    }
     for (int p = 0; p < 8; ++p)
         for (int v = 0; v < 16; ++v)
-            for (int l = 0; l < 32; ++l) im.w[kCrcWords + (p * 16 + v) * 32 + l] = kCrcHost.comb[p][v][l];
+            for (int l = 0; l < 32; ++l) im.w[kCombOffset + (p * 16 + v) * 32 + l] = kCrcHost.comb[p][v][l];
     return im;
 }
 
 __device__ const CrcImage g_crc_image = make_crc_image();
 
-// Shared-memory layout of a CTA: the table image, then one padded tile per
-// warp.
-struct Smem {
-    static __host__ __device__ constexpr size_t bytes(int warps)
-    {
-        return sizeof(uint32_t) * (kCrcWords + kCombWords) + size_t(warps) * kTileVecs * 16;
-    }
-};
+// Shared memory of a CTA: the table image, nothing else.  Every kernel
+// digests from registers, so no data is staged in shared memory, and the
+// footprint (144 KiB) leaves the SM's L1 its share for in-flight loads.
+constexpr size_t kSmemBytes = sizeof(uint32_t) * kTableWords;
 
-// s_comb must follow s_crc directly (kCrcWords words later).
-__device__ __forceinline__ void load_crc_tables(uint32_t *s_crc, uint32_t *s_comb)
+// Copies the table image to s_crc (kTableWords words) with the CTA's W * 32
+// threads; the shifted tables and the combine tables then sit at
+// s_crc + kCrcShOffset and s_crc + kCombOffset.  Each thread issues all of its
+// 16-byte loads before its first store, so the copy costs about one L2 round
+// trip (a few loads per round measured ~0.65 us a round on B300, which a
+// 16 MiB vote pays in full).
+template <int W>
+__device__ __forceinline__ void load_crc_tables(uint32_t *s_crc)
 {
-    (void)s_comb;
+    constexpr int kVecs = kTableWords / 4;
+    constexpr int kThreads = W * 32;
+    constexpr int kPer = (kVecs + kThreads - 1) / kThreads;
     const uint4 *src = reinterpret_cast<const uint4 *>(g_crc_image.w);
     uint4 *dst = reinterpret_cast<uint4 *>(s_crc);
-#pragma unroll 4
-    for (int i = threadIdx.x; i < (kCrcWords + kCombWords) / 4; i += blockDim.x) dst[i] = src[i];
+    uint4 v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = (int)threadIdx.x + k * kThreads;
+        if (i < kVecs) v[k] = src[i];
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = (int)threadIdx.x + k * kThreads;
+        if (i < kVecs) dst[i] = v[k];
+    }
 }
 
 // Per-lane constants of the table lookups.  Lane l reads copy l % 16.  In
@@ -211,21 +240,28 @@ __device__ __forceinline__ uint32_t warp_xor(uint32_t v)
     return v;
 }
 
-// Lane l's CRC of bytes [128 l, 128 l + 128) of the tile, shifted to its place
-// in the 4096-byte block and XOR-combined over the warp: the raw (zero-init)
-// register of the whole block.
-__device__ __forceinline__ uint32_t tile_crc_full(const uint4 *tile, const uint32_t *s_crc,
-                                                  const uint32_t *s_comb, const CrcLane &L, int lane)
+// The digest of a full 4 KiB block is taken in the layout of coalesced loads:
+// lane l holds the 16-byte vectors l + 32 t, t = 0..7, of the block.  The lane
+// runs its register over its vectors in order, one slicing step per word; the
+// last step of each vector except the final one uses the shifted tables, which
+// also move the register over the 496 bytes up to the lane's next vector.  The
+// lane's register then covers bytes [16 l, 16 (l + 225)) with the other lanes'
+// vectors as zeros, and the combine step moves it over the 16 (31 - l) bytes
+// that follow and XORs the lanes together (the raw register is linear in the
+// data).  No vector leaves its lane, so no staging through shared memory.
+__device__ __forceinline__ uint32_t crc_vec(const uint32_t *s_crc, const CrcLane &L, uint32_t c, const uint4 &v,
+                                            bool last)
 {
-    uint32_t c = 0;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const uint4 q = tile[9 * lane + t];
-        c = crc_step4(s_crc, L, c ^ q.x);
-        c = crc_step4(s_crc, L, c ^ q.y);
-        c = crc_step4(s_crc, L, c ^ q.z);
-        c = crc_step4(s_crc, L, c ^ q.w);
-    }
+    c = crc_step4(s_crc, L, c ^ v.x);
+    c = crc_step4(s_crc, L, c ^ v.y);
+    c = crc_step4(s_crc, L, c ^ v.z);
+    return crc_step4(last ? s_crc : s_crc + kCrcShOffset, L, c ^ v.w);
+}
+
+// The raw (zero-init) register of the whole block from the lanes' registers.
+__device__ __forceinline__ uint32_t crc_combine(const uint32_t *s_crc, uint32_t c, int lane)
+{
+    const uint32_t *s_comb = s_crc + kCombOffset;
     uint32_t r = 0;
 #pragma unroll
     for (int p = 0; p < 8; ++p) r ^= s_comb[(p * 16 + ((c >> (4 * p)) & 15u)) * 32 + lane];
@@ -246,26 +282,6 @@ __device__ __forceinline__ uint32_t shift_bytes(uint32_t c, uint32_t k)
     return c;
 }
 
-// Raw register of the first `len` (< 4096, any) bytes of the tile (a partial
-// last block): lane l digests its bytes [128 l, 128 l + 128) that lie below
-// len, four at a time and the rest one by one, and shifts its register over
-// the bytes that follow them.
-static __device__ __noinline__ uint32_t tile_crc_partial(const uint4 *tile, const uint32_t *s_crc, const CrcLane &L,
-                                                         uint32_t len, int lane)
-{
-    const uint32_t start = 128u * lane;
-    const uint32_t seg = len > start ? min(128u, len - start) : 0u;
-    const uint8_t *bytes = reinterpret_cast<const uint8_t *>(tile) + 144u * lane;
-    const uint32_t *words = reinterpret_cast<const uint32_t *>(bytes);
-    uint32_t c = 0;
-    uint32_t k = 0;
-    for (; k + 4 <= seg; k += 4) c = crc_step4(s_crc, L, c ^ words[k >> 2]);
-    for (; k < seg; ++k) c = crc_step1(s_crc, c, bytes[k]);
-    const uint32_t after = len > start + 128u ? len - start - 128u : 0u;
-    c = shift_bytes(c, after);
-    return warp_xor(c);
-}
-
 // Multiply by x^(8*4096) with the shared nibble tables (uniform across the warp).
 __device__ __forceinline__ uint32_t shift_4096(uint32_t c)
 {
@@ -274,8 +290,6 @@ __device__ __forceinline__ uint32_t shift_4096(uint32_t c)
     for (int p = 0; p < 8; ++p) r ^= g_crc.shift4096[p][(c >> (4 * p)) & 15u];
     return r;
 }
-
-__device__ __forceinline__ int tile_index(int v) { return v + (v >> 3); }
 
 // Streaming 16-byte load of read-only data that bypasses L1 allocation.
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p)
@@ -666,10 +680,10 @@ __device__ __noinline__ void closed3_rare(const TaskArgs &a, unsigned long long 
 // the block at byte offset boff) some element's replica 0 disagrees with
 // another replica.  The sub-batch is read again (one round trip; the output
 // never overlaps a replica) and voted in the exact form; its voted vectors
-// replace the fast form's in the output and in the digest tile.
+// replace the fast form's in the output, from where the lane reads them back.
 template <int K, int R, int JB>
 __device__ __noinline__ void eq0_rare(const TaskArgs &a, unsigned long long boff, int lane, int j0,
-                                      unsigned long long idx0, uint4 *tile, LaneStats<R> &st)
+                                      unsigned long long idx0, LaneStats<R> &st)
 {
     using E = Elem<K>;
     constexpr int P = 16 / E::kSize;
@@ -695,8 +709,7 @@ __device__ __noinline__ void eq0_rare(const TaskArgs &a, unsigned long long boff
             if (m) st.add_one(m, idx0 + (unsigned long long)(jj * 32 * P + e));
         }
         const int vi = lane + 32 * (j0 + jj);
-        __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
-        tile[tile_index(vi)] = yv;
+        reinterpret_cast<uint4 *>(a.out + boff)[vi] = yv;
     }
 }
 
@@ -776,12 +789,14 @@ __device__ __forceinline__ const uint8_t *rep_for_lane(const TaskArgs &a, int la
 
 // ---------------------------------------------------------------------------
 // One full 4 KiB block of one task, voted and digested by one warp.  Lanes
-// 0..R-1 first prefetch the warp's next block (b_next, if any) into L2.
+// 0..R-1 first prefetch the warp's next block (b_next, if any) into L2.  Each
+// lane keeps its eight voted vectors in registers and digests them after the
+// vote (crc_vec): digesting each vector as it is voted measured 9 % slower on
+// 3 x 256M f32, its dependent table lookups holding back the next loads.
 // ---------------------------------------------------------------------------
 template <int K, int R>
 __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long long b, unsigned long long b_next,
-                                                uint4 *tile, const uint32_t *s_crc, const uint32_t *s_comb,
-                                                const CrcLane &L, LaneStats<R> &st, int lane)
+                                                const uint32_t *s_crc, const CrcLane &L, LaneStats<R> &st, int lane)
 {
     using E = Elem<K>;
     using V = typename E::V;
@@ -793,6 +808,7 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
     const unsigned long long boff = b * kBlockBytes;
     if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);
+    uint4 yall[8];            // the lane's voted vectors l + 32 t, t = 0..7
 
 #pragma unroll
     for (int j0 = 0; j0 < 8; j0 += JB) {
@@ -835,19 +851,58 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
             }
             const int vi = lane + 32 * (j0 + jj);
             __stcs(reinterpret_cast<uint4 *>(a.out + boff) + vi, yv);
-            tile[tile_index(vi)] = yv;
+            yall[j0 + jj] = yv;
         }
         if constexpr (F == F_CLOSED2)
             if (flagged) closed2_stats<kPerVec>(flagged, idx0, st);
         if constexpr (F == F_CLOSED3)
             if (flagged) closed3_rare<K, JB>(a, boff, lane, j0, idx0, st);
-        if constexpr (F == F_EQ0)
-            if (flagged) eq0_rare<K, R, JB>(a, boff, lane, j0, idx0, tile, st);
+        if constexpr (F == F_EQ0) {
+            if (flagged) {
+                // re-voted in the exact form and stored; the lane reads its
+                // own stores back
+                eq0_rare<K, R, JB>(a, boff, lane, j0, idx0, st);
+#pragma unroll
+                for (int jj = 0; jj < JB; ++jj)
+                    yall[j0 + jj] = reinterpret_cast<const uint4 *>(a.out + boff)[lane + 32 * (j0 + jj)];
+            }
+        }
     }
-    __syncwarp();
-    const uint32_t raw = tile_crc_full(tile, s_crc, s_comb, L, lane);
+    uint32_t cc = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) cc = crc_vec(s_crc, L, cc, yall[t], t == 7);
+    const uint32_t raw = crc_combine(s_crc, cc, lane);
     if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
-    __syncwarp();
+}
+
+// One element of a partial block into a lane's register, in byte order:
+// 4-byte kinds take one slicing step, 8-byte kinds two; bytes are gathered
+// four at a time in `w` (n of them so far) and the leftover is flushed by
+// crc_flush_bytes.
+template <int K>
+__device__ __forceinline__ uint32_t crc_elem(const uint32_t *s_crc, const CrcLane &L, uint32_t c,
+                                             typename Elem<K>::V y, uint32_t &w, int &n)
+{
+    if constexpr (Elem<K>::kSize == 8) {
+        c = crc_step4(s_crc, L, c ^ (uint32_t)y);
+        return crc_step4(s_crc, L, c ^ (uint32_t)(y >> 32));
+    } else if constexpr (Elem<K>::kSize == 4) {
+        return crc_step4(s_crc, L, c ^ (uint32_t)y);
+    } else {
+        w |= (uint32_t)y << (8 * n);
+        if (++n == 4) {
+            c = crc_step4(s_crc, L, c ^ w);
+            w = 0;
+            n = 0;
+        }
+        return c;
+    }
+}
+
+__device__ __forceinline__ uint32_t crc_flush_bytes(const uint32_t *s_crc, uint32_t c, uint32_t w, int n)
+{
+    for (int k = 0; k < n; ++k) c = crc_step1(s_crc, c, (w >> (8 * k)) & 0xFFu);
+    return c;
 }
 
 // The partial last block (a.tail_bytes bytes), element by element.  Lane l
@@ -856,8 +911,8 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
 // cannot move a load above a store to the output, which may alias for all
 // it knows, so one element at a time would pay one memory latency each.
 template <int K, int R>
-__device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long long b, uint4 *tile,
-                                             const uint32_t *s_crc, const CrcLane &L, LaneStats<R> &st, int lane)
+__device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long long b, const uint32_t *s_crc,
+                                             const CrcLane &L, LaneStats<R> &st, int lane)
 {
     using E = Elem<K>;
     using V = typename E::V;
@@ -868,7 +923,8 @@ __device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long lo
     const unsigned long long boff = b * kBlockBytes;
     const uint32_t e0 = (128u * lane) / E::kSize;
     const uint32_t e1 = min(128u * (lane + 1), len) / E::kSize;
-    uint8_t *tb = reinterpret_cast<uint8_t *>(tile);
+    uint32_t cr = 0, w = 0;   // the lane's CRC register over its bytes, and gathered bytes
+    int nw = 0;
     for (uint32_t e = e0; e < e1; e += C) {
         V x[C][R];
 #pragma unroll
@@ -884,15 +940,16 @@ __device__ __noinline__ void vote_tail_block(const TaskArgs &a, unsigned long lo
             uint32_t m;
             vote_elem<K, R>(x[j], c, y, m);
             store_elem<K>(a.out + boff + (unsigned long long)(e + j) * E::kSize, y);
-            const uint32_t bo = (e + j) * E::kSize;
-            store_elem<K>(tb + tile_index(bo >> 4) * 16 + (bo & 15u), y);
+            cr = crc_elem<K>(s_crc, L, cr, y, w, nw);
             if (m) st.add_one(m, b * kEpb + e + j);
         }
     }
-    __syncwarp();
-    const uint32_t raw = tile_crc_partial(tile, s_crc, L, len, lane);
+    cr = crc_flush_bytes(s_crc, cr, w, nw);
+    // move the lane's register over the bytes after its segment, combine
+    const uint32_t start = 128u * lane;
+    cr = shift_bytes(cr, len > start + 128u ? len - start - 128u : 0u);
+    const uint32_t raw = warp_xor(cr);
     if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ shift_bytes(0xFFFFFFFFu, len));
-    __syncwarp();
 }
 
 }  // namespace ftv

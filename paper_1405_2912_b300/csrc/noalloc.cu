@@ -81,12 +81,9 @@ __global__ void __launch_bounds__(W * 32, 1) noalloc_batched_kernel(const Noallo
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *s_comb = s_crc + kCrcWords;
-    uint4 *tiles = reinterpret_cast<uint4 *>(s_comb + kCombWords);
-    load_crc_tables(s_crc, s_comb);
+    load_crc_tables<W>(s_crc);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint4 *tile = tiles + w * kTileVecs;
     CrcLane L;
     L.init(lane);
     LaneStats<R> st;
@@ -110,11 +107,11 @@ __global__ void __launch_bounds__(W * 32, 1) noalloc_batched_kernel(const Noallo
         const unsigned long long b0 = k * (unsigned long long)g.tile_blocks;
         const unsigned long long b1 = min(b0 + (unsigned long long)g.tile_blocks, a.nfull);
         for (unsigned long long b = b0; b < b1; ++b)
-            vote_full_block<K, R>(a, b, b + 1 < b1 ? b + 1 : ~0ull, tile, s_crc, s_comb, L, st, lane);
+            vote_full_block<K, R>(a, b, b + 1 < b1 ? b + 1 : ~0ull, s_crc, L, st, lane);
         if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
-            vote_tail_block<K, R>(a, a.nfull, tile, s_crc, L, ts, lane);
+            vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
             st.merge(ts);
         }
     }
@@ -267,7 +264,7 @@ static int vote_batched_noalloc(const ft_vote_desc *descs, int ntasks, int tile_
                              sizeof(unsigned long long) * ntasks, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e);
     if ((rc = launch_batch_reset(tasks_d, ntasks, cnt_d, ngroups, s)) != FT_OK) return rc;
-    const size_t smem = Smem::bytes(kNoallocWarps);
+    const size_t smem = kSmemBytes;
     for (int gi = 0; gi < ngroups; ++gi) {
         const NoallocGroup &g = groups[gi];
         if (g.total_tiles == 0) continue;

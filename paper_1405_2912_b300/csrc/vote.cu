@@ -145,12 +145,9 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *s_comb = s_crc + kCrcWords;
-    uint4 *tiles = reinterpret_cast<uint4 *>(s_comb + kCombWords);
-    load_crc_tables(s_crc, s_comb);
+    load_crc_tables<W>(s_crc);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint4 *tile = tiles + w * kTileVecs;
     CrcLane L;
     L.init(lane);
     LaneStats<R> st;
@@ -158,13 +155,12 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
     const unsigned long long step = (unsigned long long)gridDim.x * W;
     const unsigned long long gw = (unsigned long long)blockIdx.x * W + w;
     for (unsigned long long b = gw; b < a.nfull; b += step)
-        vote_full_block<K, R>(a, b, PF ? b + step : ~0ull, tile, s_crc, s_comb, L, st,
-                              lane);
+        vote_full_block<K, R>(a, b, PF ? b + step : ~0ull, s_crc, L, st, lane);
     if (a.tail_bytes && a.nfull % step == gw) {
         // the partial last block goes to the warp whose turn it would be
         LaneStats<R> ts;
         ts.init();
-        vote_tail_block<K, R>(a, a.nfull, tile, s_crc, L, ts, lane);
+        vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
         st.merge(ts);
     }
     st.flush(a.stats, lane);
@@ -174,7 +170,7 @@ template <int K, int R, int kVoteWarps, bool PF>
 static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
 {
     auto fn = vote_kernel<K, R, kVoteWarps, PF>;
-    const size_t smem = Smem::bytes(kVoteWarps);
+    const size_t smem = kSmemBytes;
     int sms = 0, per_sm = 0;
     int rc = occupancy(reinterpret_cast<const void *>(fn), kVoteWarps * 32, smem, &sms, &per_sm);
     if (rc != FT_OK) return rc;
@@ -246,7 +242,9 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)
 // ---------------------------------------------------------------------------
 // K2: digest-only CRC32C of blocks of `block_bytes` (a multiple of 4096).
 // Each warp digests whole blocks, 4 KiB chunk by chunk, and chains the chunk
-// registers with the x^(8*4096) operator.
+// registers with the x^(8*4096) operator.  A full chunk is digested from the
+// registers its coalesced loads fill (crc_vec); only a partial last chunk goes
+// through the warp's tile.
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(W * 32, 1)
@@ -255,12 +253,9 @@ __global__ void __launch_bounds__(W * 32, 1)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *s_comb = s_crc + kCrcWords;
-    uint4 *tiles = reinterpret_cast<uint4 *>(s_comb + kCombWords);
-    load_crc_tables(s_crc, s_comb);
+    load_crc_tables<W>(s_crc);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint4 *tile = tiles + w * kTileVecs;
     CrcLane L;
     L.init(lane);
     const unsigned long long step = (unsigned long long)gridDim.x * W;
@@ -283,8 +278,9 @@ __global__ void __launch_bounds__(W * 32, 1)
         have = false;
         uint32_t acc = 0;
         for (unsigned long long c = 0; c < nfull; ++c) {
+            uint4 cur[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) tile[tile_index(lane + 32 * t)] = q[t];
+            for (int t = 0; t < 8; ++t) cur[t] = q[t];
             const uint4 *next = nullptr;
             if (c + 1 < nfull) {
                 next = reinterpret_cast<const uint4 *>(buf + start + (c + 1) * kBlockBytes);
@@ -296,20 +292,22 @@ __global__ void __launch_bounds__(W * 32, 1)
 #pragma unroll
                 for (int t = 0; t < 8; ++t) q[t] = __ldcs(next + lane + 32 * t);
             }
-            __syncwarp();
-            acc = shift_4096(acc) ^ tile_crc_full(tile, s_crc, s_comb, L, lane);
-            __syncwarp();
+            uint32_t cc = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) cc = crc_vec(s_crc, L, cc, cur[t], t == 7);
+            acc = shift_4096(acc) ^ crc_combine(s_crc, cc, lane);
         }
         if (rem) {
-            const uint8_t *src = buf + start + nfull * kBlockBytes;
-            const uint32_t nvec = rem / 16;
-            for (uint32_t v = lane; v < nvec; v += 32)
-                tile[tile_index(v)] = *reinterpret_cast<const uint4 *>(src + 16 * v);
-            uint8_t *tb = reinterpret_cast<uint8_t *>(tile);
-            for (uint32_t i = nvec * 16 + lane; i < rem; i += 32) tb[tile_index(i >> 4) * 16 + (i & 15u)] = src[i];
-            __syncwarp();
-            acc = shift_bytes(acc, rem) ^ tile_crc_partial(tile, s_crc, L, rem, lane);
-            __syncwarp();
+            // partial last chunk: lane l reads its bytes [128 l, 128 l + 128)
+            // below rem itself, four at a time, and moves its register over
+            // the bytes that follow them
+            const uint8_t *src = buf + start + nfull * kBlockBytes + 128u * lane;
+            const uint32_t seg = rem > 128u * lane ? min(128u, rem - 128u * lane) : 0u;
+            uint32_t cc = 0, k = 0;
+            for (; k + 4 <= seg; k += 4) cc = crc_step4(s_crc, L, cc ^ *reinterpret_cast<const uint32_t *>(src + k));
+            for (; k < seg; ++k) cc = crc_step1(s_crc, cc, src[k]);
+            cc = shift_bytes(cc, rem > 128u * (lane + 1) ? rem - 128u * (lane + 1) : 0u);
+            acc = shift_bytes(acc, rem) ^ warp_xor(cc);
         }
         const uint32_t init = (len == block_bytes) ? init_full : shift_bytes(0xFFFFFFFFu, (uint32_t)len);
         if (lane == 0) out[b] = ~(acc ^ init);
@@ -325,7 +323,7 @@ int digest(const void *buf, unsigned long long nbytes, uint32_t block_bytes, uin
     if (!buf || !out || !aligned(buf, 16) || !aligned(out, 4)) return FT_EINVAL;
     const unsigned long long nblocks = (nbytes + block_bytes - 1) / block_bytes;
     auto fn = digest_kernel<kDigestWarps>;
-    const size_t smem = Smem::bytes(kDigestWarps);
+    const size_t smem = kSmemBytes;
     int sms = 0, per_sm = 0;
     int rc = occupancy(reinterpret_cast<const void *>(fn), kDigestWarps * 32, smem, &sms, &per_sm);
     if (rc != FT_OK) return rc;
