@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
     load_crc_tables<W>(s_crc);
     __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     CrcLane L;
     L.init(lane);
     LaneStats<R> st;
