@@ -291,6 +291,14 @@ __device__ __forceinline__ uint32_t shift_4096(uint32_t c)
     return r;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic-serialization attribute may start once the kernel before it in
+// the stream has executed pdl_release(); its pdl_wait() then blocks until that
+// kernel has completed and its writes are visible.  Without the attribute
+// both are no-ops.
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Streaming 16-byte load of read-only data that bypasses L1 allocation.
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p)
 {

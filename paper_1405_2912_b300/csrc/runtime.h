@@ -27,7 +27,6 @@ int dtype_kind(int dtype);
 int validate_desc(const ft_vote_desc *d);
 TaskArgs make_task_args(const ft_vote_desc *d);
 int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
-int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg);
 
 // One (element kind, R) group of a batch, as the batched kernel sees it.
 // tasks[t] for t in [t0, t1) belong to the group; the group's work is split

@@ -133,7 +133,14 @@ TaskArgs make_task_args(const ft_vote_desc *d)
     return a;
 }
 
-__global__ void reset_stats_kernel(ft_stats *s) { reset_stats(s, threadIdx.x); }
+// The statistics reset before a single vote.  It lets the voter kernel, which
+// is launched right after it as a programmatic dependent, start at once: the
+// voter touches the statistics only after pdl_wait().
+__global__ void reset_stats_kernel(ft_stats *s)
+{
+    pdl_release();
+    reset_stats(s, threadIdx.x);
+}
 
 // ---------------------------------------------------------------------------
 // K1: persistent single-task voter.  Warps take 4 KiB blocks in grid-stride
@@ -163,6 +170,7 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a)
         vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
         st.merge(ts);
     }
+    pdl_wait();               // the statistics reset has completed
     st.flush(a.stats, lane);
 }
 
@@ -180,7 +188,22 @@ static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch
     const unsigned long long cap = (unsigned long long)sms * per_sm;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    fn<<<(unsigned)grid, kVoteWarps * 32, smem, s>>>(a);
+    // a programmatic dependent of the statistics reset launched just before
+    // it: the kernel may start while the reset runs (it reads the replicas and
+    // writes the output and digests, which the reset does not touch) and waits
+    // for it only before its statistics flush
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kVoteWarps * 32);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, fn, a);
+    if (e != cudaSuccess) return cuda_fail(e);
     return check_launch(1);
 }
 
@@ -217,7 +240,10 @@ static int launch_vote_k(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cf
     }
 }
 
-int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
+// Only ever launched directly after the statistics reset on the same stream
+// (vote_desc): the programmatic dependency it is launched with relaxes the
+// wait on exactly that kernel.
+static int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
 {
     switch (a.kind) {
     case K_F32: return launch_vote_k<K_F32>(a, s, cfg);
