@@ -269,8 +269,8 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)
 // K2: digest-only CRC32C of blocks of `block_bytes` (a multiple of 4096).
 // Each warp digests whole blocks, 4 KiB chunk by chunk, and chains the chunk
 // registers with the x^(8*4096) operator.  A full chunk is digested from the
-// registers its coalesced loads fill (crc_vec); only a partial last chunk goes
-// through the warp's tile.
+// registers its coalesced loads fill (crc_vec); each lane reads its own
+// segment of a partial last chunk.
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(W * 32, 1)
