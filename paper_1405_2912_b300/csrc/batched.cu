@@ -270,13 +270,19 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
     tasks_dev = reinterpret_cast<const TaskArgs *>(dev + o_tasks);
 }
 
-int launch_batch(const BatchLayout &L, const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s)
+int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s)
 {
-    int rc = launch_batch_reset(L.tasks_dev, (int)L.tasks.size(), L.counters_dev, (int)gd.size(), s);
-    if (rc != FT_OK) return rc;
+    int rc = FT_OK;
     for (const GroupDev &g : gd)
         if ((rc = launch_group(g, ctas_per_sm, s)) != FT_OK) return rc;
     return FT_OK;
+}
+
+int launch_batch(const BatchLayout &L, const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s)
+{
+    const int rc = launch_batch_reset(L.tasks_dev, (int)L.tasks.size(), L.counters_dev, (int)gd.size(), s);
+    if (rc != FT_OK) return rc;
+    return launch_groups(gd, ctas_per_sm, s);
 }
 
 }  // namespace ftv

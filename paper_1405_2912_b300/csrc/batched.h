@@ -35,6 +35,10 @@ struct BatchLayout {
     void pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd);
 };
 
+// The statistics / tile-counter reset followed by the group kernels.
 int launch_batch(const BatchLayout &L, const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s);
+// The group kernels alone, for callers whose upload already carries zeroed
+// counters and initialised statistics.
+int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s);
 
 }  // namespace ftv

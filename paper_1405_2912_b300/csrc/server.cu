@@ -53,8 +53,7 @@ struct Slot {
     size_t dev_cap = 0;
     uint8_t *host = nullptr;           // batch layout staging (pinned)
     size_t host_cap = 0;
-    ft_stats *dev_stats = nullptr;     // per request of the batch
-    ft_stats *host_stats = nullptr;    // pinned copy read by the callback
+    ft_stats *host_stats = nullptr;    // pinned copy of the batch's statistics read by the callback
     ft_stats **dev_user = nullptr;     // caller stats pointers (scatter targets)
     ft_stats **host_user = nullptr;    // pinned
     int cap = 0;                       // requests per batch
@@ -123,15 +122,12 @@ int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
         sl.dev_cap = sl.host_cap = cap;
     }
     if (nreq > sl.cap) {
-        if (sl.dev_stats) cudaFree(sl.dev_stats);
         if (sl.host_stats) cudaFreeHost(sl.host_stats);
         if (sl.dev_user) cudaFree(sl.dev_user);
         if (sl.host_user) cudaFreeHost(sl.host_user);
-        sl.dev_stats = nullptr;
         sl.host_stats = nullptr;
         sl.dev_user = sl.host_user = nullptr;
         sl.cap = 0;
-        if ((e = cudaMalloc(&sl.dev_stats, sizeof(ft_stats) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         if ((e = cudaMallocHost(&sl.host_stats, sizeof(ft_stats) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         if ((e = cudaMalloc(&sl.dev_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         if ((e = cudaMallocHost(&sl.host_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
@@ -148,23 +144,37 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     for (int i = 0; i < n; ++i) args[i].stats = nullptr;   // set below, after growing
     int rc = FT_OK;
     sl.layout.build(args, s->cfg.tile_blocks);
-    rc = grow_slot(sl, sl.layout.device_bytes(), n);
+    // the statistics of the batch follow the layout in the same buffer, so
+    // that one upload carries the layout, its zeroed tile counters and the
+    // initialised statistics, and no reset kernel is needed
+    const size_t o_stats = ftv::BatchLayout::align(sl.layout.device_bytes());
+    const size_t bytes = o_stats + sizeof(ft_stats) * n;
+    rc = grow_slot(sl, bytes, n);
     if (rc != FT_OK) return rc;
+    ft_stats *dev_stats = reinterpret_cast<ft_stats *>(sl.dev + o_stats);
     // statistics of request i go to dev_stats[i]; the layout orders tasks by
     // (kind, R), so patch through its index map
-    for (size_t t = 0; t < sl.layout.tasks.size(); ++t) sl.layout.tasks[t].stats = sl.dev_stats + sl.layout.user_index[t];
-    const size_t bytes = sl.layout.device_bytes();
+    for (size_t t = 0; t < sl.layout.tasks.size(); ++t) sl.layout.tasks[t].stats = dev_stats + sl.layout.user_index[t];
     sl.layout.pack(sl.host, sl.dev, sl.gd);
+    ft_stats init;
+    for (int r = 0; r < FT_MAX_R; ++r) {
+        init.mismatch[r] = 0;
+        init.first_mismatch[r] = -1;
+    }
+    init.no_majority = 0;
+    init.first_no_majority = -1;
+    ft_stats *host_init = reinterpret_cast<ft_stats *>(sl.host + o_stats);
+    for (int i = 0; i < n; ++i) host_init[i] = init;
     cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return ftv::cuda_fail(e);
-    if ((rc = ftv::launch_batch(sl.layout, sl.gd, 0, sl.stream)) != FT_OK) return rc;
+    if ((rc = ftv::launch_groups(sl.gd, 0, sl.stream)) != FT_OK) return rc;
     if (any_user) {
         if ((e = cudaMemcpyAsync(sl.dev_user, sl.host_user, sizeof(ft_stats *) * n, cudaMemcpyHostToDevice,
                                  sl.stream)) != cudaSuccess)
             return ftv::cuda_fail(e);
-        if ((rc = ftv::launch_stats_scatter(sl.dev_stats, sl.dev_user, n, sl.stream)) != FT_OK) return rc;
+        if ((rc = ftv::launch_stats_scatter(dev_stats, sl.dev_user, n, sl.stream)) != FT_OK) return rc;
     }
-    if ((e = cudaMemcpyAsync(sl.host_stats, sl.dev_stats, sizeof(ft_stats) * n, cudaMemcpyDeviceToHost,
+    if ((e = cudaMemcpyAsync(sl.host_stats, dev_stats, sizeof(ft_stats) * n, cudaMemcpyDeviceToHost,
                              sl.stream)) != cudaSuccess)
         return ftv::cuda_fail(e);
     return FT_OK;
@@ -268,7 +278,6 @@ void free_server(ft_server *s)
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.dev) cudaFree(sl.dev);
         if (sl.host) cudaFreeHost(sl.host);
-        if (sl.dev_stats) cudaFree(sl.dev_stats);
         if (sl.host_stats) cudaFreeHost(sl.host_stats);
         if (sl.dev_user) cudaFree(sl.dev_user);
         if (sl.host_user) cudaFreeHost(sl.host_user);
@@ -302,7 +311,8 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     int rc = FT_OK;
     // size each slot for a batch that fills the whole budget
     const unsigned long long tiles = cfg->mem_budget_bytes / (2ull * 4096ull * s->cfg.tile_blocks) + cfg->max_slots;
-    const size_t guess = sizeof(ftv::TaskArgs) * cfg->max_slots + 8ull * cfg->max_slots + 4ull * tiles + 4096;
+    const size_t guess = sizeof(ftv::TaskArgs) * cfg->max_slots + 8ull * cfg->max_slots + 4ull * tiles + 4096 +
+                         sizeof(ft_stats) * (size_t)std::min(cfg->max_slots, 4096);
     for (auto &sl : s->slots) {
         if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess) {
