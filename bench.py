@@ -508,7 +508,12 @@ def run_serving(args, dev):
             nb = info.batches - info0.batches
             res[name].update({"batches": int(nb),
                               "mean_requests_per_batch": round((info.requests - info0.requests) / max(1, nb), 2),
-                              "max_batches_in_flight": int(info.max_batches_in_flight)})
+                              "max_batches_in_flight": int(info.max_batches_in_flight),
+                              # worker host time to lay out and launch a batch, and a
+                              # batch's launch -> completion span, per batch
+                              "launch_host_us_per_batch": round((info.launch_host_us - info0.launch_host_us)
+                                                                / max(1, nb), 1),
+                              "batch_span_us_mean": round((info.batch_span_us - info0.batch_span_us) / max(1, nb), 1)})
         out[label] = res
     del keep
     torch.cuda.empty_cache()

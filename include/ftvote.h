@@ -277,6 +277,8 @@ typedef struct ft_server_stats {
     int32_t  max_batches_in_flight;  /* most batches on the device at the same time      */
     int32_t  inflight_requests;      /* admitted, not yet collected                      */
     uint64_t inflight_bytes;         /* their share of the budget                        */
+    double   launch_host_us;         /* worker time spent laying out and launching batches */
+    double   batch_span_us;          /* summed launch -> completion time of the batches    */
 } ft_server_stats;
 int ft_server_info(ft_server *srv, ft_server_stats *out);
 

@@ -53,6 +53,7 @@ struct Slot {
     size_t dev_cap = 0;
     uint8_t *host = nullptr;           // batch layout staging (pinned)
     size_t host_cap = 0;
+    double launched_at = 0.0;          // worker clock when the batch began to launch
     ft_stats *host_stats = nullptr;    // pinned copy of the batch's statistics read by the callback
     ft_stats **dev_user = nullptr;     // caller stats pointers (scatter targets)
     ft_stats **host_user = nullptr;    // pinned
@@ -84,6 +85,7 @@ struct ft_server {
     // counters reported by ft_server_info
     unsigned long long batches = 0, batched_requests = 0, completed = 0;
     int busy_now = 0, busy_max = 0;
+    double launch_host_us = 0.0, batch_span_us = 0.0;
 };
 
 namespace {
@@ -102,6 +104,7 @@ void complete_slot(ft_server *s, int si, double t)
         r.done_us = t;
     }
     s->completed += sl.tickets.size();
+    s->batch_span_us += t - sl.launched_at;
     sl.tickets.clear();
     sl.busy = false;
     s->busy_now -= 1;
@@ -250,6 +253,7 @@ void worker_main(ft_server *s)
         std::vector<ft_stats *> users(args.size());
         for (size_t i = 0; i < args.size(); ++i) users[i] = s->reqs[sl.tickets[i]].user_stats;
         lk.unlock();
+        sl.launched_at = now_us();
         int rc = FT_OK;
         if (any_user) {
             rc = grow_slot(sl, 0, (int)args.size());
@@ -258,14 +262,17 @@ void worker_main(ft_server *s)
         if (rc == FT_OK) rc = launch_slot(s, free_slot, args, any_user);
         sl.status = rc;
         cudaError_t e = cudaEventRecord(sl.done, sl.stream);
+        const double launched = now_us() - sl.launched_at;
         if (e != cudaSuccess) {
             // no completion event: finish the batch here
             cudaStreamSynchronize(sl.stream);
             sl.status = ftv::cuda_fail(e);
             lk.lock();
+            s->launch_host_us += launched;
             complete_slot(s, free_slot, now_us());
         } else {
             lk.lock();
+            s->launch_host_us += launched;
         }
         idle_since = now_us();
     }
@@ -507,6 +514,8 @@ int ft_server_info(ft_server *s, ft_server_stats *out)
     out->max_batches_in_flight = s->busy_max;
     out->inflight_requests = s->inflight;
     out->inflight_bytes = s->inflight_bytes;
+    out->launch_host_us = s->launch_host_us;
+    out->batch_span_us = s->batch_span_us;
     return FT_OK;
 }
 

@@ -84,7 +84,8 @@ class ft_unit_rating(ctypes.Structure):
 class ft_server_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("requests", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("max_batches_in_flight", ctypes.c_int32), ("inflight_requests", ctypes.c_int32),
-                ("inflight_bytes", ctypes.c_uint64)]
+                ("inflight_bytes", ctypes.c_uint64), ("launch_host_us", ctypes.c_double),
+                ("batch_span_us", ctypes.c_double)]
 
 
 assert ctypes.sizeof(ft_stats) == 144

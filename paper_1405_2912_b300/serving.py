@@ -70,10 +70,12 @@ def _replay(srv, descs, arrivals_s, payload_of, start_delay_us):
                 fv.check(rc, "ft_poll_many")
             head += nd.value
     done_at = np.array([results[k].done_us for k in range(n)], dtype=np.float64)
+    submit_at = np.array([results[k].submit_us for k in range(n)], dtype=np.float64)
     errors = sum(1 for k in range(n) if results[k].status != fv.FT_OK)
     lat = done_at - arr
     span_s = (done_at.max() - arr.min()) / 1e6 if n else 0.0
-    return {"latency_us": lat, "refused": refused, "span_s": span_s, "errors": errors}
+    return {"latency_us": lat, "submit_lag_us": submit_at - arr, "server_us": done_at - submit_at,
+            "refused": refused, "span_s": span_s, "errors": errors}
 
 
 def summarize(r, bytes_per_req):
@@ -84,6 +86,11 @@ def summarize(r, bytes_per_req):
             "p99_us": round(float(np.percentile(lat, 99)), 1) if n else None,
             "mean_us": round(float(lat.mean()), 1) if n else None,
             "max_us": round(float(lat.max()), 1) if n else None,
+            # the latency split at the server's submit timestamp: the load
+            # generator's lag behind the schedule, and submit -> completion
+            "submit_lag_p50_us": round(float(np.percentile(r["submit_lag_us"], 50)), 1) if n else None,
+            "server_p50_us": round(float(np.percentile(r["server_us"], 50)), 1) if n else None,
+            "server_p99_us": round(float(np.percentile(r["server_us"], 99)), 1) if n else None,
             "req_per_s": round(n / r["span_s"], 1) if r["span_s"] > 0 else None,
             "gb_per_s": round(float(np.sum(bytes_per_req)) / r["span_s"] / 1e9, 2) if r["span_s"] > 0 else None,
             "budget_refusals": int(r["refused"]), "errors": int(r["errors"])}
