@@ -88,6 +88,10 @@ def test_server_config_validation(fv):
     assert fv.ft_server_create(None, None) == fv.FT_EINVAL
     assert fv.ft_submit(None, None, None) == fv.FT_EINVAL
     assert fv.ft_poll(None, 1, 0, None) == fv.FT_EINVAL
+    acc, nd = ctypes.c_int32(7), ctypes.c_int32(7)
+    assert fv.ft_submit_many(None, None, 0, None, ctypes.byref(acc)) == fv.FT_EINVAL
+    assert fv.ft_poll_many(None, None, 0, 0, None, ctypes.byref(nd)) == fv.FT_EINVAL
+    assert fv.ft_server_info(None, None) == fv.FT_EINVAL
     assert fv.ft_server_destroy(None) == fv.FT_EINVAL
     assert fv.ft_plan_destroy(None) == fv.FT_EINVAL
     assert fv.ft_vote_batched(None, None) == fv.FT_EINVAL
