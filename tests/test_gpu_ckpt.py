@@ -79,3 +79,45 @@ def test_restore_uploads_only_differing_blocks():
         assert dev.cpu().numpy().tobytes() == data.tobytes()
     finally:
         fv.ft_ckpt_destroy(c)
+
+
+def test_dense_changes_copy_the_whole_buffer():
+    """More than an eighth of a buffer of 64 MiB or more changed: sync and
+    restore copy the whole buffer at once (all blocks reported moved); a
+    sparse change still moves only its blocks.  Contents are checked each time."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    nbytes = (64 << 20) + 4096 * 3 + 100
+    nblocks = (nbytes + 4095) // 4096
+    rng = np.random.default_rng(4)
+    dev = torch.from_numpy(rng.integers(0, 256, size=nbytes, dtype=np.uint8)).cuda()
+    host = torch.zeros(nbytes, dtype=torch.uint8).pin_memory()
+    c = _ckpt(nbytes)
+    moved = ctypes.c_uint64()
+    sh = fv.stream_handle()
+
+    def sync():
+        fv.check(fv.ft_ckpt_sync(c, dev.data_ptr(), host.data_ptr(), sh, ctypes.byref(moved)), "sync")
+        assert torch.equal(host.cuda(), dev)
+        return moved.value
+
+    def damage(frac):
+        idx = torch.from_numpy(rng.choice(nblocks - 1, size=int((nblocks - 1) * frac), replace=False)).cuda()
+        dev[:(nblocks - 1) * 4096].view(nblocks - 1, 4096)[idx, 5] += 1
+        return int(idx.numel())
+
+    try:
+        assert sync() == nblocks                      # first sync: every block, one copy
+        damage(0.2)
+        assert sync() == nblocks                      # dense: the whole buffer
+        k = damage(0.01)
+        assert sync() == k                            # sparse: only the changed blocks
+        saved = host.clone()
+        damage(0.3)
+        fv.check(fv.ft_ckpt_restore(c, dev.data_ptr(), host.data_ptr(), sh, ctypes.byref(moved)), "restore")
+        assert moved.value == nblocks and torch.equal(dev.cpu(), saved)
+        k = damage(0.005)
+        fv.check(fv.ft_ckpt_restore(c, dev.data_ptr(), host.data_ptr(), sh, ctypes.byref(moved)), "restore")
+        assert moved.value == k and torch.equal(dev.cpu(), saved)
+    finally:
+        fv.ft_ckpt_destroy(c)
