@@ -534,7 +534,12 @@ def run_next_rows(args, dev):
     dmr (Sec. IV.D): the paper's Listing 1 task (increase an array of floats,
     here y = 1.0009765625 * x + 0.1 on 64M floats on the GPU) run once, against
     ft_dmr_run: the task twice, then the R = 2 vote with the paper's 0.1 %
-    delta.  CUDA events, median of 20."""
+    delta.  CUDA events, median of 20.
+
+    rating (Sec. IV.B, V.C): the seeded simulation of the paper's injection
+    experiment (rating_sim): mean time per result of the fault-aware choice
+    and of avoiding the faulty unit after its first fault, across fault
+    probabilities."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     out = {}
@@ -620,6 +625,17 @@ def run_next_rows(args, dev):
     single = ev_ms(lambda: task(None, 0, 0, 0))
     dmr = ev_ms(lambda: fv.check(fv.ft_dmr_run(cb, None, ctypes.byref(d), fv.stream_handle()), "ft_dmr_run"))
     s = fv.parse_stats(st, 2)
+    from paper_1405_2912_b300 import rating_sim
+    qs = [0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.65, 0.7, 0.8, 0.9]
+    rows = rating_sim.sweep(qs, rounds=4000, seed=1)
+    out["rating"] = {
+        "workload": "Sec. V.C experiment, simulated: a CPU kernel 3x faster than the GPU kernel faults with "
+                    "probability q; mean time per valid result (CPU runtime = 1), 4000 results per q",
+        "rows": rows,
+        "crossover_expected": round(1 - 1 / 3, 3),
+        "paper": "expected crossover 66 %, observed 70 %; fault-aware > 2x faster than avoiding the CPU after "
+                 "its first fault at q = 10 %",
+        "speedup_at_q10": round(rows[1]["avoid_after_first_fault"] / rows[1]["fault_aware"], 2)}
     out["dmr"] = {"workload": "y = 1.0009765625 * x + 0.1 on 2^26 f32 (two GPU kernels per run), R = 2, rel_tol 1e-3",
                   "single_ms": round(single, 3), "dmr_ms": round(dmr, 3), "overhead": round(dmr / single, 2),
                   "mismatch": s["mismatch"], "paper_overhead_range": "x1 to x3 (Sec. V.B)"}

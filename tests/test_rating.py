@@ -94,30 +94,8 @@ def test_failed_unit_only_in_check_rounds(fv):
 
 
 def _simulate(fv, q, rounds, strategy, seed):
-    """The experiment of Sec. V.C: a CPU kernel three times faster than the GPU
-    kernel faults with probability q; a faulty run is redone on the next unit.
-    Returns the mean time until a valid result."""
-    rng = np.random.default_rng(seed)
-    R = [1.0, 3.0]                   # fault-free runtimes: CPU, GPU
-    p_fault = [q, 0.0]
-    counts = [[0, 0], [0, 0]]        # valid, total
-    avoided = False
-    total = 0.0
-    for k in range(1, rounds + 1):
-        if strategy == "fault-aware":
-            order = _rank(fv, [(R[u], counts[u][0], counts[u][1]) for u in (0, 1)], k, 50) or [1]
-        else:                         # abandon the CPU after its first fault
-            order = [1] if avoided else [0, 1]
-        for u in order + [1]:
-            total += R[u]
-            ok = rng.random() >= p_fault[u]
-            counts[u][1] += 1
-            counts[u][0] += ok
-            if not ok and u == 0:
-                avoided = True
-            if ok:
-                break
-    return total / rounds
+    from paper_1405_2912_b300 import rating_sim
+    return rating_sim.simulate(q, rounds, strategy, seed)
 
 
 def test_simulated_injection_experiment(fv):
