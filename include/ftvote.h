@@ -42,8 +42,9 @@
  *   - ft_vote, ft_digest, ft_vote_many, ft_vote_batched, the registry and the
  *     rating functions may be called from several host threads at once.  A
  *     plan, a server or a checkpoint context is used by one thread at a time,
- *     except ft_submit / ft_poll / ft_server_info / ft_server_pause, which
- *     any thread may call concurrently.
+ *     except ft_submit / ft_submit_many / ft_poll / ft_poll_many /
+ *     ft_server_info / ft_server_pause, which any thread may call
+ *     concurrently.
  */
 #ifndef FTVOTE_H
 #define FTVOTE_H
