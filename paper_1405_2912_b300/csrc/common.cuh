@@ -565,10 +565,17 @@ constexpr int kSubBatch = (R <= 4) ? 4 : 2;
 // against 6.2 with 16); every other (kind, R) runs best with 16 warps and no
 // prefetch, whose extra L2 footprint costs more than it hides there (f32 R = 2:
 // 5.95 against 5.68 TB/s).
+//
+// kOverlapCrc: a lane digests each sub-batch's voted vectors while the next
+// sub-batch's loads are in flight, instead of all eight after the block.
+// Measured with 256 MB replicas: i32 R = 5 6.15 -> 6.29 TB/s, f32 R = 2
+// 6.04 -> 6.12, f32 R = 5 6.32 -> 6.35; but f32 R = 3, which keeps DRAM busy
+// with its L2 prefetch, 6.28 -> 6.05, and i32 R = 3 and u8 R = 5 lose 1-2 %.
 template <int K, int R>
 struct VotePolicy {
     static constexpr bool kPrefetch = (K == K_F32 && R == 3);
     static constexpr int kWarps = kPrefetch ? 12 : 16;
+    static constexpr bool kOverlapCrc = (R == 2) || (R >= 4 && (K == K_F32 || K == K_B4));
 };
 
 // Which fast form a (kind, R) takes in the full blocks.
@@ -799,8 +806,10 @@ __device__ __forceinline__ const uint8_t *rep_for_lane(const TaskArgs &a, int la
 // One full 4 KiB block of one task, voted and digested by one warp.  Lanes
 // 0..R-1 first prefetch the warp's next block (b_next, if any) into L2.  Each
 // lane keeps its eight voted vectors in registers and digests them after the
-// vote (crc_vec): digesting each vector as it is voted measured 9 % slower on
-// 3 x 256M f32, its dependent table lookups holding back the next loads.
+// vote (crc_vec), or, where VotePolicy says so, each sub-batch's under the
+// next sub-batch's loads.  Digesting each vector as soon as it is voted
+// measured 9 % slower on 3 x 256M f32: the table lookups then sit between the
+// vote and the next loads.
 // ---------------------------------------------------------------------------
 template <int K, int R>
 __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long long b, unsigned long long b_next,
@@ -816,7 +825,9 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
     const unsigned long long boff = b * kBlockBytes;
     if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);
+    constexpr bool kOverlap = VotePolicy<K, R>::kOverlapCrc;
     uint4 yall[8];            // the lane's voted vectors l + 32 t, t = 0..7
+    uint32_t cc = 0;          // the lane's CRC register
 
 #pragma unroll
     for (int j0 = 0; j0 < 8; j0 += JB) {
@@ -826,6 +837,13 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj)
                 v[r][jj] = ld_stream(reinterpret_cast<const uint4 *>(a.rep[r] + boff) + lane + 32 * (j0 + jj));
+        if constexpr (kOverlap) {
+            // digest the previous sub-batch while these loads are in flight
+            if (j0 > 0) {
+#pragma unroll
+                for (int jj = 0; jj < JB; ++jj) cc = crc_vec(s_crc, L, cc, yall[j0 - JB + jj], j0 - JB + jj == 7);
+            }
+        }
         uint64_t flagged = 0;
         const unsigned long long idx0 = b * kEpb + (unsigned long long)(lane + 32 * j0) * kPerVec;
 #pragma unroll
@@ -876,9 +894,13 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
             }
         }
     }
-    uint32_t cc = 0;
+    if constexpr (kOverlap) {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) cc = crc_vec(s_crc, L, cc, yall[t], t == 7);
+        for (int jj = 0; jj < JB; ++jj) cc = crc_vec(s_crc, L, cc, yall[8 - JB + jj], 8 - JB + jj == 7);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) cc = crc_vec(s_crc, L, cc, yall[t], t == 7);
+    }
     const uint32_t raw = crc_combine(s_crc, cc, lane);
     if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
 }
