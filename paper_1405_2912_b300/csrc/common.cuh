@@ -618,6 +618,12 @@ __device__ __forceinline__ void add_mask(LaneStats<R> &st, int r, uint64_t q, un
 
 // The rare paths are kept out of line so that they do not shape the fast
 // path's register allocation.
+template <int R>
+__device__ __noinline__ void record_mask(LaneStats<R> &st, uint32_t m, unsigned long long idx)
+{
+    st.add_one(m, idx);
+}
+
 template <int K, int R>
 __device__ __noinline__ void vote_elem_record(typename Elem<K>::V (&x)[R], typename Elem<K>::Ctx c,
                                               typename Elem<K>::V &y, LaneStats<R> &st, unsigned long long idx)
@@ -785,10 +791,27 @@ __device__ __forceinline__ void vote_fast(const typename Elem<K>::V (&x)[R], typ
         if (same) {
             y = x[0];
         } else {
-            typename E::V xc[R];
+            // exactly one replica's bits differ (the usual single fault): the
+            // other R - 1 >= 2 agree with replica 0, whose support is then the
+            // maximum and a majority whatever that replica compares as, so
+            // replica 0 wins and only that replica can mismatch
+            uint32_t dm = 0;
+            typename E::V xd = x[1];
 #pragma unroll
-            for (int r = 0; r < R; ++r) xc[r] = x[r];
-            vote_elem_record<K, R>(xc, c, y, st, idx);
+            for (int r = 1; r < R; ++r) {
+                const bool d = x[r] != x[0];
+                dm |= d ? (1u << r) : 0u;
+                xd = d ? x[r] : xd;
+            }
+            if ((dm & (dm - 1u)) == 0u) {
+                y = x[0];
+                if (!E::eq(E::prep(x[0], c), E::prep(xd, c), c)) record_mask<R>(st, dm, idx);
+            } else {
+                typename E::V xc[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) xc[r] = x[r];
+                vote_elem_record<K, R>(xc, c, y, st, idx);
+            }
         }
     }
 }
