@@ -114,6 +114,19 @@ typedef struct ft_vote_desc {
  * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
 int ft_vote(const ft_vote_desc *desc, ft_stream stream);
 
+/* The same vote on HOST buffers: desc->replicas, out, block_crc (or NULL)
+ * and stats are host pointers (pinned memory makes the copies direct DMA;
+ * pageable memory works, slower), with ft_vote's alignment and overlap rules.
+ * The vote runs on the current device in chunks of chunk_bytes (0 = 64 MiB; a
+ * multiple of 4096): chunk k's replicas are uploaded while chunk k-1 is voted
+ * and chunk k-2's voted bytes and digests are downloaded, on the library's own
+ * streams.  Synchronous: returns when out, block_crc and stats hold the
+ * result, which is the one ft_vote gives (statistics combined over the chunks).
+ * The library keeps 2 * (R + 1) * chunk_bytes of device staging per device
+ * between calls; calls on one device run one at a time.
+ * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
+int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes);
+
 /* CRC32C of each block_bytes-sized block of nbytes bytes at buf (device,
  * 16-byte aligned); out (device) receives ceil(nbytes / block_bytes) values,
  * the last block being partial.  block_bytes must be a multiple of 4096 in

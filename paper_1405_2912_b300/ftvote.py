@@ -123,6 +123,7 @@ ft_server_destroy = _sig("ft_server_destroy", ctypes.c_int, _P)
 ft_server_pause = _sig("ft_server_pause", ctypes.c_int, _P, ctypes.c_int32)
 ft_clock_us = _sig("ft_clock_us", ctypes.c_double)
 ft_server_info = _sig("ft_server_info", ctypes.c_int, _P, ctypes.POINTER(ft_server_stats))
+ft_vote_host = _sig("ft_vote_host", ctypes.c_int, ctypes.POINTER(ft_vote_desc), ctypes.c_uint64)
 ft_vote_many = _sig("ft_vote_many", ctypes.c_int, ctypes.POINTER(ft_vote_desc), ctypes.c_int32, _P)
 ft_vote_batched_noalloc = _sig("ft_vote_batched_noalloc", ctypes.c_int, ctypes.POINTER(ft_vote_desc),
                                ctypes.c_int32, ctypes.c_int32, _P)
