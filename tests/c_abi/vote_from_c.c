@@ -2,6 +2,7 @@
  * A plain C client of libftvote.so: no Python, no torch.  Device memory comes
  * from the CUDA runtime; the expected results are worked out here from the
  * construction of the inputs (and a bit-at-a-time CRC32C of the voted bytes).
+ * The same vote through ft_vote_host on the host arrays must agree with it.
  * Prints "C ABI OK" and exits 0 on success.
  */
 #include <math.h>
@@ -84,6 +85,21 @@ int main(void)
         CHECK(crc[b] == crc32c_bits((const unsigned char *)out + b * 4096, len), "block CRC32C");
         CHECK(dig[b] == crc[b], "ft_digest equals the fused digest");
     }
+    /* the same vote on the host arrays themselves (malloc'd, pageable), through
+       the device in 8 KiB chunks: the same voted bytes, digests and statistics */
+    ft_vote_desc hd = d;
+    float *out2 = (float *)malloc(bytes);
+    uint32_t *crc2 = (uint32_t *)malloc(4 * nblk);
+    ft_stats s2;
+    for (int r = 0; r < 3; ++r) hd.replicas[r] = h[r];
+    hd.out = out2;
+    hd.block_crc = crc2;
+    hd.stats = &s2;
+    CHECK(ft_vote_host(&hd, 8192) == FT_OK, "ft_vote_host");
+    CHECK(memcmp(out2, out, bytes) == 0, "host vote: voted values");
+    CHECK(memcmp(crc2, crc, 4 * nblk) == 0, "host vote: digests");
+    CHECK(memcmp(&s2, &s, sizeof s) == 0, "host vote: statistics");
+
     d.R = 1;
     CHECK(ft_vote(&d, NULL) == FT_EINVAL, "R = 1 rejected");
     CHECK(strcmp(ft_strerror(FT_EINVAL), "invalid argument") == 0, "ft_strerror");
