@@ -340,26 +340,36 @@ __global__ void __launch_bounds__(W * 32, 1)
     }
 }
 
-constexpr int kDigestWarps = 16;
+// Warps per CTA of the digest kernel: 20 for 4 KiB blocks (each warp's chunks
+// are then a stream of independent blocks), 16 for larger ones.  Measured on
+// 1 GiB: 4 KiB blocks 5.07 against 4.98 TB/s with 16 warps; 64 KiB blocks
+// 5.45 with 16 against 5.13 with 20 (fewer, longer blocks per warp).
+template <int W>
+static int launch_digest(const void *buf, unsigned long long nbytes, uint32_t block_bytes, uint32_t *out,
+                         cudaStream_t s)
+{
+    const unsigned long long nblocks = (nbytes + block_bytes - 1) / block_bytes;
+    auto fn = digest_kernel<W>;
+    const size_t smem = kSmemBytes;
+    int sms = 0, per_sm = 0;
+    int rc = occupancy(reinterpret_cast<const void *>(fn), W * 32, smem, &sms, &per_sm);
+    if (rc != FT_OK) return rc;
+    unsigned long long grid = (nblocks + W - 1) / W;
+    const unsigned long long cap = (unsigned long long)sms * per_sm;
+    if (grid > cap) grid = cap;
+    const uint32_t init_full = gf_mul(0xFFFFFFFFu, gf_xpow8(block_bytes));
+    fn<<<(unsigned)grid, W * 32, smem, s>>>(static_cast<const uint8_t *>(buf), nbytes, block_bytes, nblocks, out,
+                                           init_full);
+    return check_launch(1);
+}
 
 int digest(const void *buf, unsigned long long nbytes, uint32_t block_bytes, uint32_t *out, cudaStream_t s)
 {
     if (block_bytes < FT_BLOCK_BYTES || block_bytes % FT_BLOCK_BYTES || block_bytes > (1u << 24)) return FT_EINVAL;
     if (nbytes == 0) return FT_OK;
     if (!buf || !out || !aligned(buf, 16) || !aligned(out, 4)) return FT_EINVAL;
-    const unsigned long long nblocks = (nbytes + block_bytes - 1) / block_bytes;
-    auto fn = digest_kernel<kDigestWarps>;
-    const size_t smem = kSmemBytes;
-    int sms = 0, per_sm = 0;
-    int rc = occupancy(reinterpret_cast<const void *>(fn), kDigestWarps * 32, smem, &sms, &per_sm);
-    if (rc != FT_OK) return rc;
-    unsigned long long grid = (nblocks + kDigestWarps - 1) / kDigestWarps;
-    const unsigned long long cap = (unsigned long long)sms * per_sm;
-    if (grid > cap) grid = cap;
-    const uint32_t init_full = gf_mul(0xFFFFFFFFu, gf_xpow8(block_bytes));
-    fn<<<(unsigned)grid, kDigestWarps * 32, smem, s>>>(static_cast<const uint8_t *>(buf), nbytes, block_bytes,
-                                                       nblocks, out, init_full);
-    return check_launch(1);
+    if (block_bytes == FT_BLOCK_BYTES) return launch_digest<20>(buf, nbytes, block_bytes, out, s);
+    return launch_digest<16>(buf, nbytes, block_bytes, out, s);
 }
 
 }  // namespace ftv
