@@ -427,7 +427,8 @@ def device_tasks(specs, dev, config_id, threads, stats_ptr=True):
 def run_batched(args, dev, stream):
     """4096 tasks (n log-uniform 1K..4M, f32/f64/i32 40/30/30 %, R=3, one
     faulty replica in 5 % of the tasks): one graph-replayed batched vote
-    against 4096 plain ft_vote calls (ft_vote_many) on the same buffers."""
+    against 4096 plain ft_vote calls (ft_vote_many) on the same buffers, and
+    the same batch through ft_vote_batched_noalloc."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     specs = synth.cfg4_specs(ntasks=args.batched_tasks)
@@ -459,6 +460,14 @@ def run_batched(args, dev, stream):
     t_b = timed(lambda: fv.check(fv.ft_vote_batched(plan, sh), "batched"), args.batched_reps)
     launches_b = (fv.ft_launch_count() - l0) // (args.batched_reps + 3)
     t_p = timed(lambda: fv.check(fv.ft_vote_many(descs, len(specs), sh), "many"), max(2, args.batched_reps // 4))
+    # the same batch through the entry point that allocates nothing (no plan,
+    # no graph: the batch is laid out in static buffers on every call)
+    noalloc = None
+    if len(specs) <= fv.FT_NOALLOC_MAX_TASKS:
+        t_n = timed(lambda: fv.check(fv.ft_vote_batched_noalloc(descs, len(specs), tune.tile_blocks, sh), "noalloc"),
+                    args.batched_reps)
+        noalloc = {"tasks_per_s": round(len(specs) / t_n, 1), "gb_per_s": round(nbytes / t_n / 1e9, 1),
+                   "ms_per_batch": round(t_n * 1e3, 3)}
     fv.ft_plan_destroy(plan)
     del keep, stats
     torch.cuda.empty_cache()
@@ -471,6 +480,7 @@ def run_batched(args, dev, stream):
             "per_task_launches": {"tasks_per_s": round(len(specs) / t_p, 1), "gb_per_s": round(nbytes / t_p / 1e9, 1),
                                   "ms_per_batch": round(t_p * 1e3, 3)},
             "speedup_vs_per_task": round(t_p / t_b, 2),
+            "noalloc": noalloc,
             "setup_s": {"generate_upload": round(gen_s, 1), "plan_create_autotune": round(plan_s, 2)}}
 
 

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(W * 32, 1) noalloc_batched_kernel(const Noallo
         const unsigned long long b0 = k * (unsigned long long)g.tile_blocks;
         const unsigned long long b1 = min(b0 + (unsigned long long)g.tile_blocks, a.nfull);
         for (unsigned long long b = b0; b < b1; ++b)
-            vote_full_block<K, R>(a, b, b + 1 < b1 ? b + 1 : ~0ull, s_crc, L, st, lane);
+            vote_full_block<K, R>(a, b, ~0ull, s_crc, L, st, lane);   // no prefetch: as the batched kernel
         if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
