@@ -114,14 +114,19 @@ typedef struct ft_vote_desc {
  * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
 int ft_vote(const ft_vote_desc *desc, ft_stream stream);
 
-/* The same vote on HOST buffers: desc->replicas, out, block_crc (or NULL)
- * and stats are host pointers (pinned memory makes the copies direct DMA;
- * pageable memory works, slower), with ft_vote's alignment and overlap rules.
- * The vote runs on the current device in chunks of chunk_bytes (0 = 64 MiB; a
- * multiple of 4096): chunk k's replicas are uploaded while chunk k-1 is voted
- * and chunk k-2's voted bytes and digests are downloaded, on the library's own
- * streams.  Synchronous: returns when out, block_crc and stats hold the
- * result, which is the one ft_vote gives (statistics combined over the chunks).
+/* The same vote on buffers of mixed residency: each of desc->replicas[r],
+ * out, block_crc (or NULL) and stats may be host memory (pinned makes the
+ * copies direct DMA; pageable works, slower) or memory of the current device
+ * (device or managed allocation), with ft_vote's alignment and overlap rules;
+ * another device's memory is FT_EINVAL.  The vote runs on the current device
+ * in chunks of chunk_bytes (0 = 64 MiB; a multiple of 4096): chunk k's
+ * host-resident replicas are uploaded while chunk k-1 is voted and chunk k-2's
+ * voted bytes and digests are downloaded, on the library's own streams;
+ * device-resident replicas are read in place and a device-resident out or
+ * block_crc is written in place.  The call is ordered after no stream: work
+ * producing a device-resident replica must be complete when it is made.
+ * Synchronous: returns when out, block_crc and stats hold the result, which
+ * is the one ft_vote gives (statistics combined over the chunks).
  * The library keeps 2 * (R + 1) * chunk_bytes of device staging per device
  * between calls; calls on one device run one at a time.
  * Returns FT_OK, FT_EINVAL or FT_ECUDA. */

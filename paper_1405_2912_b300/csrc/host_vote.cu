@@ -1,14 +1,16 @@
-// host_vote.cu -- ft_vote_host: a vote whose replicas, output, digests and
-// statistics live in host memory (for instance a replica that a CPU kernel
-// produced in the paper's heterogeneous DMR mode, Sec. IV.D).
+// host_vote.cu -- ft_vote_host: a vote whose buffers may live in host memory
+// (for instance a replica that a CPU kernel produced in the paper's
+// heterogeneous DMR mode, Sec. IV.D), each pointer host or device.
 //
-// The vote is cut into chunks of whole 4 KiB blocks.  Chunk k's replicas are
-// uploaded on one stream while chunk k-1 is voted on a second and chunk k-2's
-// voted bytes and digests are downloaded on a third, through two sets of
-// device staging buffers, so that both directions of PCIe and the voter run
-// at once.  Each chunk is an ordinary single-task vote (vote_desc) into its
-// own statistics; the host adds the chunks' counts and takes the smallest
-// first index, shifted by each chunk's first element.
+// The vote is cut into chunks of whole 4 KiB blocks.  Chunk k's host-resident
+// replicas are uploaded on one stream while chunk k-1 is voted on a second and
+// chunk k-2's voted bytes and digests are downloaded on a third, through two
+// sets of device staging buffers, so that both directions of PCIe and the
+// voter run at once.  Device-resident replicas are read in place and a
+// device-resident output or digest array is written in place.  Each chunk is
+// an ordinary single-task vote (vote_desc) into its own statistics; the host
+// adds the chunks' counts and takes the smallest first index, shifted by each
+// chunk's first element.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -83,6 +85,20 @@ int ensure(Staging &st, size_t buf_bytes, size_t crc_words, size_t nstats)
     return FT_OK;
 }
 
+// Where a pointer lives: 1 = device or managed memory of device `dev` (used
+// in place), 0 = host memory, pinned or pageable (staged), -1 = another
+// device's memory (rejected).
+int residence(const void *p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();           // an address the runtime does not know: plain host memory
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.device == dev ? 1 : -1;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes)
@@ -102,20 +118,36 @@ extern "C" int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes)
     }
     total.no_majority = 0;
     total.first_no_majority = -1;
-    if (nbytes == 0) {
-        *desc->stats = total;
-        return FT_OK;
-    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return ftv::cuda_fail(e);
+
+    const uint8_t *const *hrep = reinterpret_cast<const uint8_t *const *>(desc->replicas);
+    uint8_t *hout = static_cast<uint8_t *>(desc->out);
+    bool rep_dev[FT_MAX_R];
+    for (int r = 0; r < R; ++r) {
+        const int where = residence(hrep[r], dev);
+        if (where < 0) return FT_EINVAL;
+        rep_dev[r] = where == 1;
+    }
+    const int out_where = residence(hout, dev);
+    const int crc_where = desc->block_crc ? residence(desc->block_crc, dev) : 0;
+    const int stats_where = residence(desc->stats, dev);
+    if (out_where < 0 || crc_where < 0 || stats_where < 0) return FT_EINVAL;
+    auto put_stats = [&]() -> int {
+        if (stats_where == 0) {
+            *desc->stats = total;
+            return FT_OK;
+        }
+        const cudaError_t pe = cudaMemcpy(desc->stats, &total, sizeof(total), cudaMemcpyHostToDevice);
+        return pe == cudaSuccess ? FT_OK : ftv::cuda_fail(pe);
+    };
+    if (nbytes == 0) return put_stats();
+
     std::lock_guard<std::mutex> lk(g_mu);
     Staging &st = g_staging[dev];
     const size_t crc_per_chunk = chunk_bytes / FT_BLOCK_BYTES;
     if ((rc = ensure(st, 2ull * (R + 1) * chunk_bytes, 2 * crc_per_chunk, nchunks)) != FT_OK) return rc;
-
-    const uint8_t *const *hrep = reinterpret_cast<const uint8_t *const *>(desc->replicas);
-    uint8_t *hout = static_cast<uint8_t *>(desc->out);
     for (uint64_t k = 0; k < nchunks; ++k) {
         const int s = (int)(k & 1);
         const uint64_t off = k * chunk_bytes;
@@ -125,8 +157,8 @@ extern "C" int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes)
         // upload: the set's replica buffers are free once chunk k-2 was voted
         if ((e = cudaStreamWaitEvent(st.up, st.voted[s], 0)) != cudaSuccess) return ftv::cuda_fail(e);
         for (int r = 0; r < R; ++r)
-            if ((e = cudaMemcpyAsync(set + (size_t)r * chunk_bytes, hrep[r] + off, len, cudaMemcpyHostToDevice,
-                                     st.up)) != cudaSuccess)
+            if (!rep_dev[r] && (e = cudaMemcpyAsync(set + (size_t)r * chunk_bytes, hrep[r] + off, len,
+                                                    cudaMemcpyHostToDevice, st.up)) != cudaSuccess)
                 return ftv::cuda_fail(e);
         if ((e = cudaEventRecord(st.uploaded[s], st.up)) != cudaSuccess) return ftv::cuda_fail(e);
         // vote: after the upload, and once chunk k-2's output has been downloaded
@@ -134,18 +166,19 @@ extern "C" int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes)
             (e = cudaStreamWaitEvent(st.comp, st.downloaded[s], 0)) != cudaSuccess)
             return ftv::cuda_fail(e);
         ft_vote_desc d = *desc;
-        for (int r = 0; r < R; ++r) d.replicas[r] = set + (size_t)r * chunk_bytes;
+        for (int r = 0; r < R; ++r) d.replicas[r] = rep_dev[r] ? hrep[r] + off : set + (size_t)r * chunk_bytes;
         d.n = len / esize;
-        d.out = set + (size_t)R * chunk_bytes;
-        d.block_crc = desc->block_crc ? dcrc : nullptr;
+        d.out = out_where == 1 ? hout + off : set + (size_t)R * chunk_bytes;
+        d.block_crc = !desc->block_crc ? nullptr : crc_where == 1 ? desc->block_crc + off / FT_BLOCK_BYTES : dcrc;
         d.stats = st.stats + k;
         if ((rc = ftv::vote_desc(&d, st.comp, nullptr)) != FT_OK) return rc;
         if ((e = cudaEventRecord(st.voted[s], st.comp)) != cudaSuccess) return ftv::cuda_fail(e);
         // download the voted bytes and the chunk's digests
         if ((e = cudaStreamWaitEvent(st.down, st.voted[s], 0)) != cudaSuccess) return ftv::cuda_fail(e);
-        if ((e = cudaMemcpyAsync(hout + off, d.out, len, cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
+        if (out_where == 0 &&
+            (e = cudaMemcpyAsync(hout + off, d.out, len, cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
             return ftv::cuda_fail(e);
-        if (desc->block_crc) {
+        if (desc->block_crc && crc_where == 0) {
             const uint64_t nblk = (len + FT_BLOCK_BYTES - 1) / FT_BLOCK_BYTES;
             if ((e = cudaMemcpyAsync(desc->block_crc + off / FT_BLOCK_BYTES, dcrc, nblk * sizeof(uint32_t),
                                      cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
@@ -172,6 +205,5 @@ extern "C" int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes)
         if (c.first_no_majority >= 0 && total.first_no_majority < 0)
             total.first_no_majority = c.first_no_majority + first_elem;
     }
-    *desc->stats = total;
-    return FT_OK;
+    return put_stats();
 }

@@ -99,3 +99,76 @@ def test_empty_and_bad_chunk():
     o = np.empty_like(a)
     d.out, d.stats = o.ctypes.data, ctypes.addressof(st)
     assert fv.ft_vote_host(ctypes.byref(d), 1000) == fv.FT_EINVAL        # not a multiple of 4096
+
+
+def _mixed_vote(reps, dtype, tol, chunk, where):
+    """ft_vote_host with each buffer placed as `where` says: a dict of
+    'rep0'..'repR-1', 'out', 'crc', 'stats' -> 'dev' | 'pinned' | 'pageable'."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    n = reps[0].size
+    np_t = oracle.NP_OF[dtype]
+    nb = n * np.dtype(np_t).itemsize
+    nblk = max(fv.n_blocks(nb), 1)
+
+    def place(arr_u8, kind):
+        t = torch.from_numpy(arr_u8.copy())
+        if kind == "dev":
+            t = t.cuda()
+        elif kind == "pinned":
+            t = t.pin_memory()
+        return t
+
+    keep = []
+    rp = []
+    for r, a in enumerate(reps):
+        t = place(np.ascontiguousarray(a).view(np.uint8), where[f"rep{r}"])
+        keep.append(t)
+        rp.append(t.data_ptr())
+    out = place(np.zeros(max(nb, 16), dtype=np.uint8), where["out"])
+    crc = place(np.zeros(4 * nblk, dtype=np.uint8), where["crc"])
+    st = place(np.zeros(ctypes.sizeof(fv.ft_stats), dtype=np.uint8), where["stats"])
+    keep += [out, crc, st]
+    torch.cuda.synchronize()                        # device inputs complete before the call
+    d = fv.ft_vote_desc()
+    for r, p in enumerate(rp):
+        d.replicas[r] = p
+    d.R, d.dtype, d.n = len(reps), fv.DTYPE[dtype], n
+    d.abs_tol, d.rel_tol = tol
+    d.out, d.block_crc, d.stats = out.data_ptr(), crc.data_ptr(), st.data_ptr()
+    fv.check(fv.ft_vote_host(ctypes.byref(d), chunk), "ft_vote_host")
+    s = fv.ft_stats.from_buffer_copy(st.cpu().numpy().tobytes())
+    R = len(reps)
+    return {"out": out.cpu().numpy()[:nb].view(np_t).copy(),
+            "block_crc": crc.cpu().numpy().view(np.uint32)[:fv.n_blocks(nb)].copy(),
+            "mismatch": list(s.mismatch)[:R], "first_mismatch": list(s.first_mismatch)[:R],
+            "no_majority": s.no_majority, "first_no_majority": s.first_no_majority}
+
+
+@pytest.mark.parametrize("where", [
+    # a device-resident replica beside host ones, the voted bytes left on the device
+    {"rep0": "dev", "rep1": "pinned", "rep2": "pageable", "out": "dev", "crc": "pinned", "stats": "dev"},
+    # every replica on the device, the result brought to the host
+    {"rep0": "dev", "rep1": "dev", "rep2": "dev", "out": "pinned", "crc": "dev", "stats": "pageable"},
+    # host replicas, device outputs
+    {"rep0": "pinned", "rep1": "pinned", "rep2": "pinned", "out": "dev", "crc": "dev", "stats": "pinned"},
+])
+def test_mixed_residency(where):
+    rng = np.random.default_rng(11)
+    n = (2 * 8192) // 4 * 5 + 777                  # five chunks of two blocks and a ragged sixth
+    base = synth.lognormal(rng, n, "f32")
+    reps = [base.copy() for _ in range(3)]
+    for r in range(3):
+        idx = np.flatnonzero(rng.random(n) < 0.02)
+        synth.bit_flip(reps[r], idx, rng.integers(0, 32, size=idx.size))
+    tol = synth.TOL["f32"]
+    ref = oracle.vote(reps, "f32", *tol)
+    _check(_mixed_vote(reps, "f32", tol, 2 * 8192, where), ref)
+
+
+def test_mixed_residency_empty_device_stats():
+    where = {"rep0": "dev", "rep1": "pinned", "rep2": "dev", "out": "dev", "crc": "dev", "stats": "dev"}
+    reps = [np.zeros(0, dtype=np.float32) for _ in range(3)]
+    got = _mixed_vote(reps, "f32", (1e-6, 1e-5), 0, where)
+    assert [int(x) for x in got["mismatch"]] == [0, 0, 0]
+    assert [int(x) for x in got["first_mismatch"]] == [-1, -1, -1] and int(got["first_no_majority"]) == -1
