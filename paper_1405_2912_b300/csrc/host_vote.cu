@@ -148,51 +148,62 @@ extern "C" int ft_vote_host(const ft_vote_desc *desc, uint64_t chunk_bytes)
     Staging &st = g_staging[dev];
     const size_t crc_per_chunk = chunk_bytes / FT_BLOCK_BYTES;
     if ((rc = ensure(st, 2ull * (R + 1) * chunk_bytes, 2 * crc_per_chunk, nchunks)) != FT_OK) return rc;
-    for (uint64_t k = 0; k < nchunks; ++k) {
-        const int s = (int)(k & 1);
-        const uint64_t off = k * chunk_bytes;
-        const uint64_t len = std::min<uint64_t>(chunk_bytes, nbytes - off);
-        uint8_t *set = st.buf + (size_t)s * (R + 1) * chunk_bytes;
-        uint32_t *dcrc = st.crc + (size_t)s * crc_per_chunk;
-        // upload: the set's replica buffers are free once chunk k-2 was voted
-        if ((e = cudaStreamWaitEvent(st.up, st.voted[s], 0)) != cudaSuccess) return ftv::cuda_fail(e);
-        for (int r = 0; r < R; ++r)
-            if (!rep_dev[r] && (e = cudaMemcpyAsync(set + (size_t)r * chunk_bytes, hrep[r] + off, len,
-                                                    cudaMemcpyHostToDevice, st.up)) != cudaSuccess)
+    // The pipeline; an error part-way leaves copies in flight into the caller's
+    // buffers, so every exit below waits for the three streams first.
+    auto pipeline = [&]() -> int {
+        for (uint64_t k = 0; k < nchunks; ++k) {
+            const int s = (int)(k & 1);
+            const uint64_t off = k * chunk_bytes;
+            const uint64_t len = std::min<uint64_t>(chunk_bytes, nbytes - off);
+            uint8_t *set = st.buf + (size_t)s * (R + 1) * chunk_bytes;
+            uint32_t *dcrc = st.crc + (size_t)s * crc_per_chunk;
+            // upload: the set's replica buffers are free once chunk k-2 was voted
+            if ((e = cudaStreamWaitEvent(st.up, st.voted[s], 0)) != cudaSuccess) return ftv::cuda_fail(e);
+            for (int r = 0; r < R; ++r)
+                if (!rep_dev[r] && (e = cudaMemcpyAsync(set + (size_t)r * chunk_bytes, hrep[r] + off, len,
+                                                        cudaMemcpyHostToDevice, st.up)) != cudaSuccess)
+                    return ftv::cuda_fail(e);
+            if ((e = cudaEventRecord(st.uploaded[s], st.up)) != cudaSuccess) return ftv::cuda_fail(e);
+            // vote: after the upload, and once chunk k-2's output has been downloaded
+            if ((e = cudaStreamWaitEvent(st.comp, st.uploaded[s], 0)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st.comp, st.downloaded[s], 0)) != cudaSuccess)
                 return ftv::cuda_fail(e);
-        if ((e = cudaEventRecord(st.uploaded[s], st.up)) != cudaSuccess) return ftv::cuda_fail(e);
-        // vote: after the upload, and once chunk k-2's output has been downloaded
-        if ((e = cudaStreamWaitEvent(st.comp, st.uploaded[s], 0)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(st.comp, st.downloaded[s], 0)) != cudaSuccess)
-            return ftv::cuda_fail(e);
-        ft_vote_desc d = *desc;
-        for (int r = 0; r < R; ++r) d.replicas[r] = rep_dev[r] ? hrep[r] + off : set + (size_t)r * chunk_bytes;
-        d.n = len / esize;
-        d.out = out_where == 1 ? hout + off : set + (size_t)R * chunk_bytes;
-        d.block_crc = !desc->block_crc ? nullptr : crc_where == 1 ? desc->block_crc + off / FT_BLOCK_BYTES : dcrc;
-        d.stats = st.stats + k;
-        if ((rc = ftv::vote_desc(&d, st.comp, nullptr)) != FT_OK) return rc;
-        if ((e = cudaEventRecord(st.voted[s], st.comp)) != cudaSuccess) return ftv::cuda_fail(e);
-        // download the voted bytes and the chunk's digests
-        if ((e = cudaStreamWaitEvent(st.down, st.voted[s], 0)) != cudaSuccess) return ftv::cuda_fail(e);
-        if (out_where == 0 &&
-            (e = cudaMemcpyAsync(hout + off, d.out, len, cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
-            return ftv::cuda_fail(e);
-        if (desc->block_crc && crc_where == 0) {
-            const uint64_t nblk = (len + FT_BLOCK_BYTES - 1) / FT_BLOCK_BYTES;
-            if ((e = cudaMemcpyAsync(desc->block_crc + off / FT_BLOCK_BYTES, dcrc, nblk * sizeof(uint32_t),
-                                     cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
+            ft_vote_desc d = *desc;
+            for (int r = 0; r < R; ++r) d.replicas[r] = rep_dev[r] ? hrep[r] + off : set + (size_t)r * chunk_bytes;
+            d.n = len / esize;
+            d.out = out_where == 1 ? hout + off : set + (size_t)R * chunk_bytes;
+            d.block_crc = !desc->block_crc ? nullptr : crc_where == 1 ? desc->block_crc + off / FT_BLOCK_BYTES : dcrc;
+            d.stats = st.stats + k;
+            if ((rc = ftv::vote_desc(&d, st.comp, nullptr)) != FT_OK) return rc;
+            if ((e = cudaEventRecord(st.voted[s], st.comp)) != cudaSuccess) return ftv::cuda_fail(e);
+            // download the voted bytes and the chunk's digests
+            if ((e = cudaStreamWaitEvent(st.down, st.voted[s], 0)) != cudaSuccess) return ftv::cuda_fail(e);
+            if (out_where == 0 &&
+                (e = cudaMemcpyAsync(hout + off, d.out, len, cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
                 return ftv::cuda_fail(e);
+            if (desc->block_crc && crc_where == 0) {
+                const uint64_t nblk = (len + FT_BLOCK_BYTES - 1) / FT_BLOCK_BYTES;
+                if ((e = cudaMemcpyAsync(desc->block_crc + off / FT_BLOCK_BYTES, dcrc, nblk * sizeof(uint32_t),
+                                         cudaMemcpyDeviceToHost, st.down)) != cudaSuccess)
+                    return ftv::cuda_fail(e);
+            }
+            if ((e = cudaEventRecord(st.downloaded[s], st.down)) != cudaSuccess) return ftv::cuda_fail(e);
         }
-        if ((e = cudaEventRecord(st.downloaded[s], st.down)) != cudaSuccess) return ftv::cuda_fail(e);
+        // the chunks' statistics, after the last vote
+        if ((e = cudaMemcpyAsync(st.host_stats, st.stats, nchunks * sizeof(ft_stats), cudaMemcpyDeviceToHost,
+                                 st.comp)) != cudaSuccess)
+            return ftv::cuda_fail(e);
+        if ((e = cudaStreamSynchronize(st.comp)) != cudaSuccess || (e = cudaStreamSynchronize(st.down)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st.up)) != cudaSuccess)
+            return ftv::cuda_fail(e);
+        return FT_OK;
+    };
+    if ((rc = pipeline()) != FT_OK) {
+        cudaStreamSynchronize(st.up);
+        cudaStreamSynchronize(st.comp);
+        cudaStreamSynchronize(st.down);
+        return rc;
     }
-    // the chunks' statistics, after the last vote
-    if ((e = cudaMemcpyAsync(st.host_stats, st.stats, nchunks * sizeof(ft_stats), cudaMemcpyDeviceToHost,
-                             st.comp)) != cudaSuccess)
-        return ftv::cuda_fail(e);
-    if ((e = cudaStreamSynchronize(st.comp)) != cudaSuccess || (e = cudaStreamSynchronize(st.down)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st.up)) != cudaSuccess)
-        return ftv::cuda_fail(e);
     for (uint64_t k = 0; k < nchunks; ++k) {
         const ft_stats &c = st.host_stats[k];
         const int64_t first_elem = (int64_t)(k * chunk_bytes / esize);
