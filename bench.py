@@ -506,7 +506,7 @@ def run_serving(args, dev):
         per_req = np.array([(specs[r.payload].R + 1) * r.n * (4 if r.dtype == "f32" else 8) for r in reqs])
         res = {"offered_gb_per_s": round(float(per_req.sum()) / args.serve_seconds / 1e9, 1)}
         for name, slots, cap in (("continuous_batching", 4096, 1 << 30), ("unbatched", 1, 0)):
-            cfg = fv.ft_server_config(int(40e9), slots, 3, 8, 0, cap)
+            cfg = fv.ft_server_config(int(40e9), slots, 3, 0, 0, cap)
             srv = ctypes.c_void_p()
             fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
             try:

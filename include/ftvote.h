@@ -195,7 +195,9 @@ int ft_plan_destroy(ft_plan *plan);
  * buffers: the call allocates nothing, neither with cudaMalloc nor on the
  * host.  The caller still owns every input and output buffer.
  *   ntasks       0 .. FT_NOALLOC_MAX_TASKS; more is rejected with FT_EINVAL.
- *   tile_blocks  4 KiB blocks per work tile, 1 .. 64 (0 = 8).
+ *   tile_blocks  4 KiB blocks per work tile, 1 .. 64; 0 = automatic: 8,
+ *                halved while the batch would make fewer tiles than the
+ *                kernel has warps in one wave, down to 1.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  All calls
  * share the array and it keeps the last call's contents (counters and
@@ -216,7 +218,9 @@ typedef struct ft_server_config {
                                    collected requests of (R+1) * n * sizeof(dtype) */
     int32_t  max_slots;         /* most requests packed into one batch (1..65536) */
     int32_t  streams;           /* batches in flight at once (1..8)               */
-    int32_t  tile_blocks;       /* batched-kernel tile (0 = 8)                     */
+    int32_t  tile_blocks;       /* batched-kernel tile, 1..64; 0 = automatic per batch:
+                                   8, halved while the batch would make fewer tiles
+                                   than the kernel has warps in one wave, down to 1 */
     int32_t  max_inflight;      /* most admitted, not yet collected requests (0 = 65536) */
     uint64_t max_batch_bytes;   /* a batch takes waiting requests (oldest first) while their
                                    (R+1)*n*sizeof(dtype) bytes stay within this, and at least

@@ -198,8 +198,8 @@ static int scratch_address(int dev, unsigned char **out)
 static int vote_batched_noalloc(const ft_vote_desc *descs, int ntasks, int tile_blocks, cudaStream_t s)
 {
     if (ntasks < 0 || ntasks > kNoallocMaxTasks || (ntasks > 0 && !descs)) return FT_EINVAL;
-    if (tile_blocks == 0) tile_blocks = 8;
-    if (tile_blocks < 1 || tile_blocks > 64) return FT_EINVAL;
+    const bool auto_tile = tile_blocks == 0;
+    if (tile_blocks < 0 || tile_blocks > 64) return FT_EINVAL;
     for (int i = 0; i < ntasks; ++i) {
         const int rc = validate_desc(&descs[i]);
         if (rc != FT_OK) return rc;
@@ -236,6 +236,17 @@ static int vote_batched_noalloc(const ft_vote_desc *descs, int ntasks, int tile_
         const int k = group_key(dtype_kind(descs[i].dtype), descs[i].R);
         tasks_h[fill[k]++] = make_task_args(&descs[i]);
     }
+    const size_t smem = kSmemBytes;
+    if (auto_tile) {
+        unsigned long long total = 0;
+        for (int i = 0; i < ntasks; ++i) total += tasks_h[i].nfull + (tasks_h[i].tail_bytes ? 1 : 0);
+        const TaskArgs &a0 = tasks_h[0];
+        const void *fn = noalloc_kernel(a0.kind, a0.R);
+        if (!fn) return FT_EINVAL;
+        int sms = 0, per_sm = 0;
+        if ((rc = noalloc_occupancy(dev, group_key(a0.kind, a0.R), fn, smem, &sms, &per_sm)) != FT_OK) return rc;
+        tile_blocks = auto_tile_blocks(total, (unsigned long long)sms * per_sm * kNoallocWarps);
+    }
     for (int k = 0; k < kNoallocMaxGroups; ++k) {
         if (!count[k]) continue;
         unsigned long long tiles = 0;
@@ -264,7 +275,6 @@ static int vote_batched_noalloc(const ft_vote_desc *descs, int ntasks, int tile_
                              sizeof(unsigned long long) * ntasks, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e);
     if ((rc = launch_batch_reset(tasks_d, ntasks, cnt_d, ngroups, s)) != FT_OK) return rc;
-    const size_t smem = kSmemBytes;
     for (int gi = 0; gi < ngroups; ++gi) {
         const NoallocGroup &g = groups[gi];
         if (g.total_tiles == 0) continue;

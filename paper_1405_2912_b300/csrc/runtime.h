@@ -51,6 +51,12 @@ int launch_batch_reset(const TaskArgs *tasks, int ntasks, unsigned long long *co
 int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s);
 // Resident CTAs per SM of the batched kernel for (kind, R) and the SM count.
 int group_occupancy(int kind, int R, int *sms, int *per_sm);
+// Tile size of a batch whose caller left it to the library: 8 blocks, halved
+// while the batch's total_blocks would make fewer tiles than the kernel has
+// warps in one wave (wave_warps), so that a small batch is spread over as
+// many warps as it has blocks instead of being walked block after block by a
+// few warps.
+int auto_tile_blocks(unsigned long long total_blocks, unsigned long long wave_warps);
 // Copy stats of tasks[i] to user[i] where user[i] is not null (server).
 int launch_stats_scatter(const ft_stats *src, ft_stats *const *dst, int n, cudaStream_t s);
 int digest(const void *buf, unsigned long long nbytes, uint32_t block_bytes, uint32_t *out, cudaStream_t s);

@@ -69,6 +69,7 @@ struct Slot {
 
 struct ft_server {
     ft_server_config cfg{};
+    bool auto_tile = false;            // tile size chosen per batch (configured as 0)
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_work;   // worker: new requests, a free slot, stop
@@ -146,7 +147,16 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     const int n = (int)args.size();
     for (int i = 0; i < n; ++i) args[i].stats = nullptr;   // set below, after growing
     int rc = FT_OK;
-    sl.layout.build(args, s->cfg.tile_blocks);
+    int tile = s->cfg.tile_blocks;
+    if (s->auto_tile) {
+        unsigned long long total = 0;
+        for (const ftv::TaskArgs &a : args) total += a.nfull + (a.tail_bytes ? 1 : 0);
+        int sms = 0, per_sm = 0;
+        if ((rc = ftv::group_occupancy(args[0].kind, args[0].R, &sms, &per_sm)) != FT_OK) return rc;
+        // each of the batches in flight at once gets about its share of a wave
+        tile = ftv::auto_tile_blocks(total, (unsigned long long)sms * per_sm * ftv::kBatchWarps / s->slots.size());
+    }
+    sl.layout.build(args, tile);
     // the statistics of the batch follow the layout in the same buffer, so
     // that one upload carries the layout, its zeroed tile counters and the
     // initialised statistics, and no reset kernel is needed
@@ -307,6 +317,7 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     ft_server *s = new (std::nothrow) ft_server();
     if (!s) return FT_ENOMEM;
     s->cfg = *cfg;
+    s->auto_tile = cfg->tile_blocks == 0;
     if (s->cfg.tile_blocks == 0) s->cfg.tile_blocks = 8;
     if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 65536;
     cudaError_t e = cudaGetDevice(&s->device);

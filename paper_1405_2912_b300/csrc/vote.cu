@@ -56,6 +56,13 @@ int occupancy(const void *fn, int threads, size_t smem, int *sms, int *per_sm)
     return FT_OK;
 }
 
+int auto_tile_blocks(unsigned long long total_blocks, unsigned long long wave_warps)
+{
+    int tb = 8;
+    while (tb > 1 && total_blocks < (unsigned long long)tb * wave_warps) tb >>= 1;
+    return tb;
+}
+
 size_t dtype_size(int dtype)
 {
     switch (dtype) {

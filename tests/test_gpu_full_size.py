@@ -74,7 +74,7 @@ def test_serving_full_stream():
         d = fv.ft_vote_desc.from_buffer_copy(t.desc)
         d.stats = None
         descs.append(d)
-    cfg = fv.ft_server_config(int(40e9), 4096, 3, 8, 0)
+    cfg = fv.ft_server_config(int(40e9), 4096, 3, 0, 0)
     srv = ctypes.c_void_p()
     fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
     seen = []

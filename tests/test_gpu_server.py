@@ -41,7 +41,8 @@ def _stats_dict(st, R):
             "no_majority": int(st.no_majority), "first_no_majority": int(st.first_no_majority)}
 
 
-def test_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("tile", [8, 0])          # 0: tile size chosen per batch
+def test_same_alone_and_in_the_mix(tile):
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     probs = _requests()
@@ -51,7 +52,7 @@ def test_same_alone_and_in_the_mix():
     torch.cuda.synchronize()
     alone_res = [t.result() for t in alone]
     mixed = [DevTask(p) for p in probs]
-    srv = _server(budget=1 << 34)
+    srv = _server(budget=1 << 34, tile=tile)
     try:
         tickets = []
         for i, t in enumerate(mixed):
@@ -218,7 +219,7 @@ def test_concurrent_clients():
         d = fv.ft_vote_desc.from_buffer_copy(t.desc)
         d.stats = None
         descs.append(d)
-    srv = _server(budget=1 << 33, max_slots=8, streams=3)
+    srv = _server(budget=1 << 33, max_slots=8, streams=3, tile=0)
     errors = []
 
     def client(cid):
