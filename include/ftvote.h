@@ -234,7 +234,7 @@ typedef struct ft_result {
     uint64_t n;
     ft_stats stats;             /* copy of the request's statistics              */
     double   submit_us;         /* host clock (monotonic, microseconds) at submit */
-    double   done_us;           /* host clock when the batch's completion callback ran */
+    double   done_us;           /* host clock when the worker saw the batch complete */
 } ft_result;
 
 /* Start a server: one host thread that packs admitted requests into batches

@@ -54,7 +54,7 @@ struct Slot {
     uint8_t *host = nullptr;           // batch layout staging (pinned)
     size_t host_cap = 0;
     double launched_at = 0.0;          // worker clock when the batch began to launch
-    ft_stats *host_stats = nullptr;    // pinned copy of the batch's statistics read by the callback
+    ft_stats *host_stats = nullptr;    // pinned copy of the batch's statistics, read once the event completes
     ft_stats **dev_user = nullptr;     // caller stats pointers (scatter targets)
     ft_stats **host_user = nullptr;    // pinned
     int cap = 0;                       // requests per batch

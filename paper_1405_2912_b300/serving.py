@@ -3,7 +3,7 @@
 A load generator for the serving form: it submits each request at its
 scheduled arrival time (host monotonic clock of the library, ft_clock_us),
 retries requests that the budget refuses, collects results in arrival order,
-and reports latency = completion time (the batch's completion callback) minus
+and reports latency = completion time (when the server's worker saw the batch complete) minus
 the scheduled arrival time, so that queueing behind the budget and in the
 server both count.  Each pass of its loop submits every request that has
 arrived with one ft_submit_many and retires the finished ones with one
