@@ -332,6 +332,29 @@ def run_ours(args, problem, ws, rank, local):
                "h2d_bytes_per_step": R * nbytes, "d2h_bytes_per_step": nbytes + 4 * nblk + 144 * nchunks,
                "steps": args.e2e_steps, "call": "ft_vote_host (pinned host buffers, 64 MiB chunks)",
                "matches_device_vote": bool(np.array_equal(crc_h.numpy(), crc.cpu().numpy()))}
+        # the same copies alone, in the same chunks, uploads on one stream and
+        # the download on another: the ceiling that the link sets for e2e (the
+        # device replicas are overwritten with their own contents)
+        up_s, down_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+        def copies():
+            for off in range(0, nbytes, chunk):
+                end = min(off + chunk, nbytes)
+                with torch.cuda.stream(up_s):
+                    for r in range(R):
+                        reps[r][off:end].copy_(host[r][off:end], non_blocking=True)
+                with torch.cuda.stream(down_s):
+                    out_h[off:end].copy_(out[off:end], non_blocking=True)
+            torch.cuda.synchronize()
+
+        copies()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            copies()
+        t_copy = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e["copy_only_gb_per_s"] = round(bytes_step * args.e2e_steps * ws / t_copy / 1e9, 3)
+        e2e["frac_of_copy_only"] = round(e2e["value"] / e2e["copy_only_gb_per_s"], 3)
         del host, out_h
 
     s = fv.parse_stats(stats, R)
