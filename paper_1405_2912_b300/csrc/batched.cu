@@ -18,6 +18,29 @@
 
 namespace ftv {
 
+// The last CTA of a group to finish copies the group's statistics to the
+// host-mapped array.  Every thread's statistics atomics are made visible at
+// device scope before its CTA is counted, and the last CTA reads the final
+// values from L2.
+__device__ __noinline__ void copy_out_if_last(const GroupDev &g)
+{
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(g.done_ctas, 1ull) == (unsigned long long)gridDim.x - 1ull;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    constexpr int kWords = (int)(sizeof(ft_stats) / 8);
+    const int n = (g.t1 - g.t0) * kWords;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const ft_stats *src = g.tasks[g.t0 + i / kWords].stats;
+        const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long *>(src) + i % kWords);
+        reinterpret_cast<unsigned long long *>(g.stats_out + (src - g.stats_base))[i % kWords] = v;
+    }
+    __threadfence_system();
+}
+
 // ---------------------------------------------------------------------------
 // K3: persistent batched voter for one (kind, R) group.  A warp claims the
 // next tile with one atomic, looks up its task in the tile map, votes the
@@ -66,6 +89,7 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
         }
     }
     if (cur >= 0) st.flush(cur_stats, lane);
+    if (g.done_ctas) copy_out_if_last(g);
 }
 
 template <int K, int R>
@@ -205,7 +229,7 @@ void BatchLayout::build(const std::vector<TaskArgs> &in, int tile_blocks)
 size_t BatchLayout::device_bytes() const
 {
     return align(sizeof(TaskArgs) * tasks.size()) + align(8 * tile_first.size()) + align(4 * tile_task.size()) +
-           align(8 * groups.size());
+           align(16 * groups.size());
 }
 
 // Packs the layout into `host` (device_bytes() long) as it must appear at
@@ -223,7 +247,7 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
     if (!tasks.empty()) std::memcpy(host + o_tasks, tasks.data(), sizeof(TaskArgs) * tasks.size());
     if (!tile_first.empty()) std::memcpy(host + o_first, tile_first.data(), 8 * tile_first.size());
     if (!tile_task.empty()) std::memcpy(host + o_map, tile_task.data(), 4 * tile_task.size());
-    std::memset(host + o_cnt, 0, 8 * groups.size());
+    std::memset(host + o_cnt, 0, 16 * groups.size());   // tile counters, then done counters
     gd.clear();
     for (size_t i = 0; i < groups.size(); ++i) {
         const GroupHost &gh = groups[i];
@@ -234,9 +258,12 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
         g.tile_first = reinterpret_cast<const unsigned long long *>(dev + o_first);
         g.total_tiles = gh.tiles;
         g.counter = reinterpret_cast<unsigned long long *>(dev + o_cnt) + i;
+        g.done_ctas = nullptr;     // no copy-out unless the caller sets it
         g.tile_blocks = tile_blocks_;
         g.kind = gh.kind;
         g.R = gh.R;
+        g.t0 = gh.t0;
+        g.t1 = gh.t1;
         gd.push_back(g);
     }
     counters_dev = reinterpret_cast<unsigned long long *>(dev + o_cnt);

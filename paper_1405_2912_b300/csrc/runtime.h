@@ -32,15 +32,22 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
 // tasks[t] for t in [t0, t1) belong to the group; the group's work is split
 // into total_tiles tiles of tile_blocks 4 KiB blocks; tile_task[g] is the task
 // of the group's tile g and tile_first[t] the group tile where task t starts.
+// With done_ctas set, the group's last CTA to finish copies the statistics of
+// tasks t0..t1-1 to stats_out[tasks[t].stats - stats_base] (host-mapped
+// memory), so that no download follows the kernel.
 struct GroupDev {
     const TaskArgs *tasks;
     const uint32_t *tile_task;
     const unsigned long long *tile_first;
     unsigned long long total_tiles;
-    unsigned long long *counter;   // tile dispenser, zeroed by the reset kernel
+    unsigned long long *counter;     // tile dispenser, zeroed before the launch
+    unsigned long long *done_ctas;   // CTAs finished, zeroed before the launch; nullptr: no copy-out
+    const ft_stats *stats_base;      // the batch's statistics array (device)
+    ft_stats *stats_out;             // its host-mapped copy
     int32_t tile_blocks;
     int32_t kind;
     int32_t R;
+    int32_t t0, t1;
     int32_t pad_;
 };
 

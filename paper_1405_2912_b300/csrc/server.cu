@@ -1,4 +1,4 @@
-// server.cpp -- the serving form of the voter: continuous batching of vote
+// server.cu -- the serving form of the voter: continuous batching of vote
 // requests (ft_server_create / ft_submit / ft_poll).
 //
 // Requests are admitted against a device-memory budget: each one holds
@@ -48,13 +48,14 @@ struct Request {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;        // recorded after the batch's last copy
+    cudaEvent_t done = nullptr;        // recorded after the batch's kernels
     uint8_t *dev = nullptr;            // batch layout (device)
     size_t dev_cap = 0;
     uint8_t *host = nullptr;           // batch layout staging (pinned)
     size_t host_cap = 0;
     double launched_at = 0.0;          // worker clock when the batch began to launch
     ft_stats *host_stats = nullptr;    // pinned copy of the batch's statistics, read once the event completes
+    ft_stats *host_stats_dev = nullptr;   // the same memory as the device addresses it
     ft_stats **dev_user = nullptr;     // caller stats pointers (scatter targets)
     ft_stats **host_user = nullptr;    // pinned
     int cap = 0;                       // requests per batch
@@ -133,6 +134,9 @@ int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
         sl.dev_user = sl.host_user = nullptr;
         sl.cap = 0;
         if ((e = cudaMallocHost(&sl.host_stats, sizeof(ft_stats) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
+        if ((e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&sl.host_stats_dev), sl.host_stats, 0)) !=
+            cudaSuccess)
+            return ftv::cuda_fail(e);
         if ((e = cudaMalloc(&sl.dev_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         if ((e = cudaMallocHost(&sl.host_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         sl.cap = nreq;
@@ -178,6 +182,17 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     init.first_no_majority = -1;
     ft_stats *host_init = reinterpret_cast<ft_stats *>(sl.host + o_stats);
     for (int i = 0; i < n; ++i) host_init[i] = init;
+    // each group kernel's last CTA writes the group's statistics straight into
+    // the slot's pinned array, so no download follows the kernels; a group
+    // without tiles (only empty requests) launches nothing and is filled here
+    for (size_t gi = 0; gi < sl.gd.size(); ++gi) {
+        ftv::GroupDev &g = sl.gd[gi];
+        g.done_ctas = sl.layout.counters_dev + sl.gd.size() + gi;
+        g.stats_base = dev_stats;
+        g.stats_out = sl.host_stats_dev;
+        if (g.total_tiles == 0)
+            for (int t = g.t0; t < g.t1; ++t) sl.host_stats[sl.layout.user_index[t]] = init;
+    }
     cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return ftv::cuda_fail(e);
     if ((rc = ftv::launch_groups(sl.gd, 0, sl.stream)) != FT_OK) return rc;
@@ -187,9 +202,6 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
             return ftv::cuda_fail(e);
         if ((rc = ftv::launch_stats_scatter(dev_stats, sl.dev_user, n, sl.stream)) != FT_OK) return rc;
     }
-    if ((e = cudaMemcpyAsync(sl.host_stats, dev_stats, sizeof(ft_stats) * n, cudaMemcpyDeviceToHost,
-                             sl.stream)) != cudaSuccess)
-        return ftv::cuda_fail(e);
     return FT_OK;
 }
 

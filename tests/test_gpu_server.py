@@ -323,3 +323,47 @@ def test_bulk_submit_and_poll():
         sd = _stats_dict(results[k].stats, p.R)
         for key, v in sd.items():
             assert np.array_equal(np.asarray(got[key]), np.asarray(v)), (k, key)
+
+
+def test_empty_requests_and_groups_in_a_batch():
+    """One batch holding empty requests: inside a (kind, R) group that has
+    tiles (the group kernel's last CTA copies their statistics out) and as the
+    whole of a group (no kernel runs for it; the server fills them).  Every
+    empty request reads (0, -1) for all replicas; the others match the
+    oracle."""
+    from paper_1405_2912_b300 import ftvote as fv
+    specs = [synth.TaskSpec(0, "f64", 5, False, 41), synth.TaskSpec(5000, "f32", 3, True, 42),
+             synth.TaskSpec(0, "f64", 5, False, 43), synth.TaskSpec(0, "i32", 4, False, 44),
+             synth.TaskSpec(3001, "f64", 5, True, 45)]
+    probs = [synth.task_problem(s, config_id=5, ulp_frac=0.05, flip_rate=1e-3) for s in specs]
+    tasks = [DevTask(p) for p in probs]
+    srv = _server(budget=1 << 32, tile=0)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tickets = []
+        for t in tasks:
+            d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+            d.stats = None
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)) == fv.FT_OK
+            tickets.append(tk.value)
+        fv.ft_server_pause(srv, 0)
+        for p, tk in zip(probs, tickets):
+            r = fv.ft_result()
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+            assert r.status == fv.FT_OK
+            if p.n == 0:
+                assert list(r.stats.mismatch) == [0] * 8 and list(r.stats.first_mismatch) == [-1] * 8
+                assert r.stats.no_majority == 0 and r.stats.first_no_majority == -1
+            else:
+                ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+                got = _stats_dict(r.stats, p.R)
+                assert list(got["mismatch"]) == [int(x) for x in ref["mismatch"]]
+                assert list(got["first_mismatch"]) == [int(x) for x in ref["first_mismatch"]]
+                assert got["no_majority"] == int(ref["no_majority"])
+                assert got["first_no_majority"] == int(ref["first_no_majority"])
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        assert info.batches == 1
+    finally:
+        fv.ft_server_destroy(srv)
