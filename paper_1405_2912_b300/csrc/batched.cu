@@ -18,44 +18,84 @@
 
 namespace ftv {
 
-// The last CTA of a group to finish copies the group's statistics to the
-// host-mapped array.  Every thread's statistics atomics are made visible at
-// device scope before its CTA is counted, and the last CTA reads the final
-// values from L2.
-__device__ __noinline__ void copy_out_if_last(const GroupDev &g)
+// Statistics hand-off at the end of a group kernel.  The last CTA to finish
+// copies the statistics of tasks[0..ntasks) to stats_out[tasks[t].stats -
+// stats_base] (host-mapped memory), so that no download follows the kernel.
+// Every thread's statistics atomics are made visible at device scope before
+// its CTA is counted, and the last CTA reads the final values from L2.  With
+// `reset`, it then puts each statistics word back to its initial value and
+// zeroes the tile and done counters, leaving the buffers ready for the next
+// launch without an upload.
+struct CopyOut {
+    unsigned long long *done_ctas;
+    unsigned long long *counter;   // zeroed when reset
+    const TaskArgs *tasks;
+    int ntasks;
+    bool reset;
+    const ft_stats *stats_base;
+    ft_stats *stats_out;
+};
+
+__device__ __noinline__ void copy_out_if_last(const CopyOut &c)
 {
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(g.done_ctas, 1ull) == (unsigned long long)gridDim.x - 1ull;
+    if (threadIdx.x == 0) s_last = atomicAdd(c.done_ctas, 1ull) == (unsigned long long)gridDim.x - 1ull;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    constexpr int kWords = (int)(sizeof(ft_stats) / 8);
-    const int n = (g.t1 - g.t0) * kWords;
+    constexpr int kWords = (int)(sizeof(ft_stats) / 8);   // mismatch[8], first[8], no_majority, first
+    static_assert(kWords == 2 * FT_MAX_R + 2, "ft_stats layout");
+    const int n = c.ntasks * kWords;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const ft_stats *src = g.tasks[g.t0 + i / kWords].stats;
-        const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long *>(src) + i % kWords);
-        reinterpret_cast<unsigned long long *>(g.stats_out + (src - g.stats_base))[i % kWords] = v;
+        const int w = i % kWords;
+        ft_stats *src = c.tasks[i / kWords].stats;
+        unsigned long long *word = reinterpret_cast<unsigned long long *>(src) + w;
+        reinterpret_cast<unsigned long long *>(c.stats_out + (src - c.stats_base))[w] = __ldcg(word);
+        if (c.reset) *word = (w < FT_MAX_R || w == 2 * FT_MAX_R) ? 0ull : ~0ull;   // counts 0, first indices -1
+    }
+    if (c.reset && threadIdx.x == 0) {
+        *c.counter = 0;
+        *c.done_ctas = 0;
     }
     __threadfence_system();
 }
 
+// The task of a tile: from the tile map (plans and large batches) ...
+struct MapLookup {
+    const TaskArgs *tasks;
+    const uint32_t *tile_task;
+    const unsigned long long *tile_first;
+    __device__ __forceinline__ int task_of(unsigned long long tg, int) const { return (int)tile_task[tg]; }
+};
+
+// ... or, for a batch of at most 32 tasks, as the last task whose first tile
+// is at or before it (one ballot; an empty task shares its first tile with
+// the next task, or starts at the group's end, so it is never picked).
+struct ScanLookup {
+    const TaskArgs *tasks;
+    const unsigned long long *tile_first;
+    int ntasks;
+    __device__ __forceinline__ int task_of(unsigned long long tg, int lane) const
+    {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, lane < ntasks && tile_first[lane] <= tg);
+        return 31 - __clz((int)m);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // K3: persistent batched voter for one (kind, R) group.  A warp claims the
-// next tile with one atomic, looks up its task in the tile map, votes the
-// tile's 4 KiB blocks (and the task's partial last block when the tile holds
-// it), and flushes its per-task statistics whenever it moves to another task.
-// Tiles are claimed in increasing order, so a warp meets each task's blocks in
-// increasing order and the first index it sees per replica is its minimum.
+// next tile with one atomic, looks up its task, votes the tile's 4 KiB blocks
+// (and the task's partial last block when the tile holds it), and flushes its
+// per-task statistics whenever it moves to another task.  Tiles are claimed
+// in increasing order, so a warp meets each task's blocks in increasing order
+// and the first index it sees per replica is its minimum.
 // ---------------------------------------------------------------------------
-template <int K, int R, int W>
-__global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
+template <int K, int R, class Lookup>
+__device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long *counter, unsigned long long total_tiles,
+                                           int tile_blocks, const uint32_t *s_crc)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    load_crc_tables<W>(s_crc);
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     CrcLane L;
     L.init(lane);
@@ -65,23 +105,23 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
     ft_stats *cur_stats = nullptr;
     for (;;) {
         unsigned long long tg = 0;
-        if (lane == 0) tg = atomicAdd(g.counter, 1ull);
+        if (lane == 0) tg = atomicAdd(counter, 1ull);
         tg = __shfl_sync(0xFFFFFFFFu, tg, 0);
-        if (tg >= g.total_tiles) break;
-        const int t = (int)g.tile_task[tg];
-        const TaskArgs a = g.tasks[t];
+        if (tg >= total_tiles) break;
+        const int t = lk.task_of(tg, lane);
+        const TaskArgs a = lk.tasks[t];
         if (t != cur) {
             if (cur >= 0) st.flush(cur_stats, lane);
             st.init();
             cur = t;
             cur_stats = a.stats;
         }
-        const unsigned long long k = tg - g.tile_first[t];
-        const unsigned long long b0 = k * (unsigned long long)g.tile_blocks;
-        const unsigned long long b1 = min(b0 + (unsigned long long)g.tile_blocks, a.nfull);
+        const unsigned long long k = tg - lk.tile_first[t];
+        const unsigned long long b0 = k * (unsigned long long)tile_blocks;
+        const unsigned long long b1 = min(b0 + (unsigned long long)tile_blocks, a.nfull);
         for (unsigned long long b = b0; b < b1; ++b)
             vote_full_block<K, R>(a, b, ~0ull, s_crc, L, st, lane);
-        if (a.tail_bytes && a.nfull / g.tile_blocks == k) {
+        if (a.tail_bytes && a.nfull / tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
             vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
@@ -89,38 +129,64 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
         }
     }
     if (cur >= 0) st.flush(cur_stats, lane);
-    if (g.done_ctas) copy_out_if_last(g);
+}
+
+template <int K, int R, int W>
+__global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
+    load_crc_tables<W>(s_crc);
+    __syncthreads();
+    vote_tiles<K, R>(MapLookup{g.tasks, g.tile_task, g.tile_first}, g.counter, g.total_tiles, g.tile_blocks, s_crc);
+    if (g.done_ctas)
+        copy_out_if_last(CopyOut{g.done_ctas, nullptr, g.tasks + g.t0, g.t1 - g.t0, false, g.stats_base, g.stats_out});
+}
+
+// The same voter for a small batch whose whole group travels in the kernel
+// parameters (no upload); its counters and statistics are left reset for the
+// next launch by the last CTA.
+template <int K, int R, int W>
+__global__ void __launch_bounds__(W * 32, 1) batched_small_kernel(const __grid_constant__ SmallGroup g)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
+    load_crc_tables<W>(s_crc);
+    __syncthreads();
+    vote_tiles<K, R>(ScanLookup{g.tasks, g.tile_first, g.ntasks}, g.counter, g.total_tiles, g.tile_blocks, s_crc);
+    copy_out_if_last(CopyOut{g.done_ctas, g.counter, g.tasks, g.ntasks, true, g.stats_base, g.stats_out});
 }
 
 template <int K, int R>
-static const void *group_fn()
+static const void *group_fn(bool small)
 {
-    return reinterpret_cast<const void *>(batched_kernel<K, R, kBatchWarps>);
+    return small ? reinterpret_cast<const void *>(batched_small_kernel<K, R, kBatchWarps>)
+                 : reinterpret_cast<const void *>(batched_kernel<K, R, kBatchWarps>);
 }
 
 template <int K>
-static const void *group_fn_k(int R)
+static const void *group_fn_k(int R, bool small)
 {
     switch (R) {
-    case 2: return group_fn<K, 2>();
-    case 3: return group_fn<K, 3>();
-    case 4: return group_fn<K, 4>();
-    case 5: return group_fn<K, 5>();
-    case 6: return group_fn<K, 6>();
-    case 7: return group_fn<K, 7>();
-    case 8: return group_fn<K, 8>();
+    case 2: return group_fn<K, 2>(small);
+    case 3: return group_fn<K, 3>(small);
+    case 4: return group_fn<K, 4>(small);
+    case 5: return group_fn<K, 5>(small);
+    case 6: return group_fn<K, 6>(small);
+    case 7: return group_fn<K, 7>(small);
+    case 8: return group_fn<K, 8>(small);
     default: return nullptr;
     }
 }
 
-static const void *group_kernel(int kind, int R)
+static const void *group_kernel(int kind, int R, bool small = false)
 {
     switch (kind) {
-    case K_F32: return group_fn_k<K_F32>(R);
-    case K_F64: return group_fn_k<K_F64>(R);
-    case K_B1: return group_fn_k<K_B1>(R);
-    case K_B4: return group_fn_k<K_B4>(R);
-    case K_B8: return group_fn_k<K_B8>(R);
+    case K_F32: return group_fn_k<K_F32>(R, small);
+    case K_F64: return group_fn_k<K_F64>(R, small);
+    case K_B1: return group_fn_k<K_B1>(R, small);
+    case K_B4: return group_fn_k<K_B4>(R, small);
+    case K_B8: return group_fn_k<K_B8>(R, small);
     default: return nullptr;
     }
 }
@@ -133,23 +199,44 @@ int group_occupancy(int kind, int R, int *sms, int *per_sm)
     return occupancy(fn, warps * 32, kSmemBytes, sms, per_sm);
 }
 
+// One CTA per kBatchWarps tiles, at most the resident CTAs of the whole GPU.
+static int group_grid(const void *fn, unsigned long long total_tiles, int ctas_per_sm, unsigned *grid)
+{
+    int sms = 0, per_sm = 0;
+    const int rc = occupancy(fn, kBatchWarps * 32, kSmemBytes, &sms, &per_sm);
+    if (rc != FT_OK) return rc;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    unsigned long long g = (unsigned long long)sms * per_sm;
+    const unsigned long long need = (total_tiles + kBatchWarps - 1) / kBatchWarps;
+    *grid = (unsigned)(g < need ? g : need);
+    return FT_OK;
+}
+
 int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
 {
     const void *fn = group_kernel(g.kind, g.R);
     if (!fn) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
-    const int warps = kBatchWarps;
-    const size_t smem = kSmemBytes;
-    int sms = 0, per_sm = 0;
-    int rc = occupancy(fn, warps * 32, smem, &sms, &per_sm);
+    unsigned grid = 0;
+    const int rc = group_grid(fn, g.total_tiles, ctas_per_sm, &grid);
     if (rc != FT_OK) return rc;
-    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-    unsigned long long grid = (unsigned long long)sms * per_sm;
-    const unsigned long long need = (g.total_tiles + warps - 1) / warps;
-    if (grid > need) grid = need;
     GroupDev arg = g;
     void *params[] = {&arg};
-    const cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(warps * 32), params, smem, s);
+    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBatchWarps * 32), params, kSmemBytes, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return check_launch(1);
+}
+
+int launch_small_group(const SmallGroup &g, cudaStream_t s)
+{
+    const void *fn = group_kernel(g.kind, g.R, true);
+    if (!fn || g.ntasks < 1 || g.ntasks > kSmallTasks) return FT_EINVAL;
+    if (g.total_tiles == 0) return FT_OK;
+    unsigned grid = 0;
+    const int rc = group_grid(fn, g.total_tiles, 0, &grid);
+    if (rc != FT_OK) return rc;
+    void *params[] = {const_cast<SmallGroup *>(&g)};
+    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBatchWarps * 32), params, kSmemBytes, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return check_launch(1);
 }

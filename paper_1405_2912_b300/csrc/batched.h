@@ -17,6 +17,27 @@ namespace ftv {
 // against 0.599 M (6.25 TB/s) with the single-task shapes.
 constexpr int kBatchWarps = 16;
 
+// A (kind, R) group of a small batch, passed whole as the kernel parameter:
+// no upload precedes the launch.  tile_first[t] is task t's first tile (an
+// empty task's equals the next one's); counter and done_ctas are zero and
+// each task's statistics (0, -1) at launch, and the group kernel's last CTA
+// leaves them so after copying the statistics to stats_out.
+constexpr int kSmallTasks = 16;
+struct SmallGroup {
+    TaskArgs tasks[kSmallTasks];
+    unsigned long long tile_first[kSmallTasks];
+    unsigned long long total_tiles;
+    unsigned long long *counter;
+    unsigned long long *done_ctas;
+    const ft_stats *stats_base;      // the slot's statistics array (device)
+    ft_stats *stats_out;             // its host-mapped copy
+    int32_t ntasks;
+    int32_t tile_blocks;
+    int32_t kind;
+    int32_t R;
+};
+int launch_small_group(const SmallGroup &g, cudaStream_t s);
+
 struct GroupHost {
     int kind, R;
     int t0, t1;                 // task range in the ordered table

@@ -64,7 +64,30 @@ struct Slot {
     std::vector<unsigned long long> tickets;
     ftv::BatchLayout layout;
     std::vector<ftv::GroupDev> gd;
+    // small batches (at most kSmallTasks requests, no caller statistics
+    // pointers) travel in the kernel parameters; their tile and done counters
+    // and statistics live here, left reset by each group kernel's last CTA
+    uint8_t *small_area = nullptr;
+    unsigned long long *small_cnt = nullptr;   // 2 per group: tile counter, done counter
+    ft_stats *small_stats = nullptr;           // one per request
+    bool small_dirty = true;                   // re-initialise before the next small batch
+    bool last_small = false;                   // the batch in flight took the small path
 };
+
+constexpr size_t kSmallCntBytes = 2 * ftv::kSmallTasks * sizeof(unsigned long long);
+constexpr size_t kSmallAreaBytes = kSmallCntBytes + ftv::kSmallTasks * sizeof(ft_stats);
+
+ft_stats initial_stats()
+{
+    ft_stats st;
+    for (int r = 0; r < FT_MAX_R; ++r) {
+        st.mismatch[r] = 0;
+        st.first_mismatch[r] = -1;
+    }
+    st.no_majority = 0;
+    st.first_no_majority = -1;
+    return st;
+}
 
 }  // namespace
 
@@ -105,6 +128,7 @@ void complete_slot(ft_server *s, int si, double t)
         r.done = true;
         r.done_us = t;
     }
+    if (sl.last_small && sl.status != FT_OK) sl.small_dirty = true;
     s->completed += sl.tickets.size();
     s->batch_span_us += t - sl.launched_at;
     sl.tickets.clear();
@@ -144,6 +168,62 @@ int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
     return FT_OK;
 }
 
+// A small batch: its (kind, R) groups are launched with their tasks in the
+// kernel parameters, so nothing is uploaded, and the statistics come back
+// through the group kernels' last CTAs.
+int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int tile)
+{
+    const int n = (int)args.size();
+    cudaError_t e;
+    if (sl.small_dirty) {
+        // first use, or a failed batch may have left counters or statistics set
+        uint8_t init[kSmallAreaBytes];
+        std::memset(init, 0, kSmallCntBytes);
+        const ft_stats st = initial_stats();
+        for (int i = 0; i < ftv::kSmallTasks; ++i) std::memcpy(init + kSmallCntBytes + i * sizeof(ft_stats), &st, sizeof st);
+        if ((e = cudaMemcpyAsync(sl.small_area, init, kSmallAreaBytes, cudaMemcpyHostToDevice, sl.stream)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(sl.stream)) != cudaSuccess)
+            return ftv::cuda_fail(e);
+        sl.small_dirty = false;
+    }
+    int order[ftv::kSmallTasks];
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order, order + n, [&](int x, int y) {
+        return std::make_pair(args[x].kind, args[x].R) < std::make_pair(args[y].kind, args[y].R);
+    });
+    ftv::SmallGroup g;
+    int gi = 0;
+    for (int i = 0; i < n; ++gi) {
+        std::memset(&g, 0, sizeof g);
+        g.kind = args[order[i]].kind;
+        g.R = args[order[i]].R;
+        g.tile_blocks = tile;
+        for (; i < n && args[order[i]].kind == g.kind && args[order[i]].R == g.R; ++i) {
+            ftv::TaskArgs a = args[order[i]];
+            a.stats = sl.small_stats + order[i];
+            g.tile_first[g.ntasks] = g.total_tiles;
+            g.total_tiles += (a.nfull + (a.tail_bytes ? 1 : 0) + tile - 1) / tile;
+            g.tasks[g.ntasks++] = a;
+        }
+        g.counter = sl.small_cnt + 2 * gi;
+        g.done_ctas = sl.small_cnt + 2 * gi + 1;
+        g.stats_base = sl.small_stats;
+        g.stats_out = sl.host_stats_dev;
+        if (g.total_tiles == 0) {
+            // only empty requests: no kernel, and their statistics stay initial
+            for (int t = 0; t < g.ntasks; ++t) sl.host_stats[g.tasks[t].stats - sl.small_stats] = initial_stats();
+            continue;
+        }
+        const int rc = ftv::launch_small_group(g, sl.stream);
+        if (rc != FT_OK) {
+            sl.small_dirty = true;
+            return rc;
+        }
+    }
+    return FT_OK;
+}
+
 // Launch the requests `tickets` as one batch on slot `si` (lock not held).
 int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any_user)
 {
@@ -160,6 +240,11 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
         // each of the batches in flight at once gets about its share of a wave
         tile = ftv::auto_tile_blocks(total, (unsigned long long)sms * per_sm * ftv::kBatchWarps / s->slots.size());
     }
+    sl.last_small = n <= ftv::kSmallTasks && !any_user;
+    if (sl.last_small) {
+        if ((rc = grow_slot(sl, 0, n)) != FT_OK) return rc;
+        return launch_small_batch(sl, args, tile);
+    }
     sl.layout.build(args, tile);
     // the statistics of the batch follow the layout in the same buffer, so
     // that one upload carries the layout, its zeroed tile counters and the
@@ -173,13 +258,7 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     // (kind, R), so patch through its index map
     for (size_t t = 0; t < sl.layout.tasks.size(); ++t) sl.layout.tasks[t].stats = dev_stats + sl.layout.user_index[t];
     sl.layout.pack(sl.host, sl.dev, sl.gd);
-    ft_stats init;
-    for (int r = 0; r < FT_MAX_R; ++r) {
-        init.mismatch[r] = 0;
-        init.first_mismatch[r] = -1;
-    }
-    init.no_majority = 0;
-    init.first_no_majority = -1;
+    const ft_stats init = initial_stats();
     ft_stats *host_init = reinterpret_cast<ft_stats *>(sl.host + o_stats);
     for (int i = 0; i < n; ++i) host_init[i] = init;
     // each group kernel's last CTA writes the group's statistics straight into
@@ -310,6 +389,7 @@ void free_server(ft_server *s)
         if (sl.host_stats) cudaFreeHost(sl.host_stats);
         if (sl.dev_user) cudaFree(sl.dev_user);
         if (sl.host_user) cudaFreeHost(sl.host_user);
+        if (sl.small_area) cudaFree(sl.small_area);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     delete s;
@@ -350,6 +430,12 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
             break;
         }
         if ((rc = grow_slot(sl, guess, std::min(cfg->max_slots, 4096))) != FT_OK) break;
+        if ((e = cudaMalloc(&sl.small_area, kSmallAreaBytes)) != cudaSuccess) {
+            rc = ftv::cuda_fail(e);
+            break;
+        }
+        sl.small_cnt = reinterpret_cast<unsigned long long *>(sl.small_area);
+        sl.small_stats = reinterpret_cast<ft_stats *>(sl.small_area + kSmallCntBytes);
     }
     if (rc != FT_OK) {
         free_server(s);

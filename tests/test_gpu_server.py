@@ -325,12 +325,16 @@ def test_bulk_submit_and_poll():
             assert np.array_equal(np.asarray(got[key]), np.asarray(v)), (k, key)
 
 
-def test_empty_requests_and_groups_in_a_batch():
+@pytest.mark.parametrize("user_stats", [False, True])
+def test_empty_requests_and_groups_in_a_batch(user_stats):
     """One batch holding empty requests: inside a (kind, R) group that has
     tiles (the group kernel's last CTA copies their statistics out) and as the
     whole of a group (no kernel runs for it; the server fills them).  Every
     empty request reads (0, -1) for all replicas; the others match the
-    oracle."""
+    oracle.  Without caller statistics pointers the batch travels in the
+    kernel parameters; one caller pointer sends it through the upload path
+    (and that request's device statistics must match too).  The same server
+    then takes a second batch, on counters and statistics left reset."""
     from paper_1405_2912_b300 import ftvote as fv
     specs = [synth.TaskSpec(0, "f64", 5, False, 41), synth.TaskSpec(5000, "f32", 3, True, 42),
              synth.TaskSpec(0, "f64", 5, False, 43), synth.TaskSpec(0, "i32", 4, False, 44),
@@ -339,31 +343,36 @@ def test_empty_requests_and_groups_in_a_batch():
     tasks = [DevTask(p) for p in probs]
     srv = _server(budget=1 << 32, tile=0)
     try:
-        fv.ft_server_pause(srv, 1)
-        tickets = []
-        for t in tasks:
-            d = fv.ft_vote_desc.from_buffer_copy(t.desc)
-            d.stats = None
-            tk = ctypes.c_uint64()
-            assert fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)) == fv.FT_OK
-            tickets.append(tk.value)
-        fv.ft_server_pause(srv, 0)
-        for p, tk in zip(probs, tickets):
-            r = fv.ft_result()
-            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
-            assert r.status == fv.FT_OK
-            if p.n == 0:
-                assert list(r.stats.mismatch) == [0] * 8 and list(r.stats.first_mismatch) == [-1] * 8
-                assert r.stats.no_majority == 0 and r.stats.first_no_majority == -1
-            else:
+        for rnd in range(2):
+            fv.ft_server_pause(srv, 1)
+            tickets = []
+            for i, t in enumerate(tasks):
+                d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+                if not (user_stats and i == 1):
+                    d.stats = None
+                tk = ctypes.c_uint64()
+                assert fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)) == fv.FT_OK
+                tickets.append(tk.value)
+            fv.ft_server_pause(srv, 0)
+            for i, (p, tk) in enumerate(zip(probs, tickets)):
+                r = fv.ft_result()
+                assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+                assert r.status == fv.FT_OK
+                if p.n == 0:
+                    assert list(r.stats.mismatch) == [0] * 8 and list(r.stats.first_mismatch) == [-1] * 8
+                    assert r.stats.no_majority == 0 and r.stats.first_no_majority == -1
+                    continue
                 ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
-                got = _stats_dict(r.stats, p.R)
-                assert list(got["mismatch"]) == [int(x) for x in ref["mismatch"]]
-                assert list(got["first_mismatch"]) == [int(x) for x in ref["first_mismatch"]]
-                assert got["no_majority"] == int(ref["no_majority"])
-                assert got["first_no_majority"] == int(ref["first_no_majority"])
-        info = fv.ft_server_stats()
-        fv.ft_server_info(srv, ctypes.byref(info))
-        assert info.batches == 1
+                views = [_stats_dict(r.stats, p.R)]
+                if user_stats and i == 1:
+                    views.append(tasks[i].result())
+                for got in views:
+                    assert [int(x) for x in got["mismatch"]] == [int(x) for x in ref["mismatch"]]
+                    assert [int(x) for x in got["first_mismatch"]] == [int(x) for x in ref["first_mismatch"]]
+                    assert int(got["no_majority"]) == int(ref["no_majority"])
+                    assert int(got["first_no_majority"]) == int(ref["first_no_majority"])
+            info = fv.ft_server_stats()
+            fv.ft_server_info(srv, ctypes.byref(info))
+            assert info.batches == rnd + 1
     finally:
         fv.ft_server_destroy(srv)
