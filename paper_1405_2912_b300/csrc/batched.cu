@@ -199,26 +199,28 @@ int group_occupancy(int kind, int R, int *sms, int *per_sm)
     return occupancy(fn, warps * 32, kSmemBytes, sms, per_sm);
 }
 
-// One CTA per kBatchWarps tiles, at most the resident CTAs of the whole GPU.
-static int group_grid(const void *fn, unsigned long long total_tiles, int ctas_per_sm, unsigned *grid)
+// One CTA per kBatchWarps tiles, at most the resident CTAs of the whole GPU
+// and at most max_ctas (0 = no limit).
+static int group_grid(const void *fn, unsigned long long total_tiles, int ctas_per_sm, int max_ctas, unsigned *grid)
 {
     int sms = 0, per_sm = 0;
     const int rc = occupancy(fn, kBatchWarps * 32, kSmemBytes, &sms, &per_sm);
     if (rc != FT_OK) return rc;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     unsigned long long g = (unsigned long long)sms * per_sm;
+    if (max_ctas > 0 && g > (unsigned long long)max_ctas) g = (unsigned long long)max_ctas;
     const unsigned long long need = (total_tiles + kBatchWarps - 1) / kBatchWarps;
     *grid = (unsigned)(g < need ? g : need);
     return FT_OK;
 }
 
-int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
+int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s, int max_ctas)
 {
     const void *fn = group_kernel(g.kind, g.R);
     if (!fn) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
     unsigned grid = 0;
-    const int rc = group_grid(fn, g.total_tiles, ctas_per_sm, &grid);
+    const int rc = group_grid(fn, g.total_tiles, ctas_per_sm, max_ctas, &grid);
     if (rc != FT_OK) return rc;
     GroupDev arg = g;
     void *params[] = {&arg};
@@ -227,13 +229,13 @@ int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s)
     return check_launch(1);
 }
 
-int launch_small_group(const SmallGroup &g, cudaStream_t s)
+int launch_small_group(const SmallGroup &g, cudaStream_t s, int max_ctas)
 {
     const void *fn = group_kernel(g.kind, g.R, true);
     if (!fn || g.ntasks < 1 || g.ntasks > kSmallTasks) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
     unsigned grid = 0;
-    const int rc = group_grid(fn, g.total_tiles, 0, &grid);
+    const int rc = group_grid(fn, g.total_tiles, 0, max_ctas, &grid);
     if (rc != FT_OK) return rc;
     void *params[] = {const_cast<SmallGroup *>(&g)};
     const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBatchWarps * 32), params, kSmemBytes, s);
@@ -357,11 +359,11 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
     tasks_dev = reinterpret_cast<const TaskArgs *>(dev + o_tasks);
 }
 
-int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s)
+int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s, int max_ctas)
 {
     int rc = FT_OK;
     for (const GroupDev &g : gd)
-        if ((rc = launch_group(g, ctas_per_sm, s)) != FT_OK) return rc;
+        if ((rc = launch_group(g, ctas_per_sm, s, max_ctas)) != FT_OK) return rc;
     return FT_OK;
 }
 

@@ -36,7 +36,7 @@ struct SmallGroup {
     int32_t kind;
     int32_t R;
 };
-int launch_small_group(const SmallGroup &g, cudaStream_t s);
+int launch_small_group(const SmallGroup &g, cudaStream_t s, int max_ctas = 0);
 
 struct GroupHost {
     int kind, R;
@@ -66,6 +66,6 @@ struct BatchLayout {
 int launch_batch(const BatchLayout &L, const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s);
 // The group kernels alone, for callers whose upload already carries zeroed
 // counters and initialised statistics.
-int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s);
+int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s, int max_ctas = 0);
 
 }  // namespace ftv

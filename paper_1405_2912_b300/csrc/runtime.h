@@ -55,7 +55,7 @@ struct GroupDev {
 int launch_batch_reset(const TaskArgs *tasks, int ntasks, unsigned long long *counters, int ncounters,
                        cudaStream_t s);
 // Launch the persistent batched voter for one group.
-int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s);
+int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s, int max_ctas = 0);
 // Resident CTAs per SM of the batched kernel for (kind, R) and the SM count.
 int group_occupancy(int kind, int R, int *sms, int *per_sm);
 // Tile size of a batch whose caller left it to the library: 8 blocks, halved
