@@ -264,7 +264,7 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     }
     sl.layout.build(args, tile);
     // the statistics of the batch follow the layout in the same buffer, so
-    // that one upload carries the layout, its zeroed tile counters and the
+    // that one upload carries the layout, its zeroed tile and done counters and the
     // initialised statistics, and no reset kernel is needed
     const size_t o_stats = ftv::BatchLayout::align(sl.layout.device_bytes());
     const size_t bytes = o_stats + sizeof(ft_stats) * n;
