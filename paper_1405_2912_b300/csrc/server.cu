@@ -72,6 +72,47 @@ struct Slot {
     ft_stats *small_stats = nullptr;           // one per request
     bool small_dirty = true;                   // re-initialise before the next small batch
     bool last_small = false;                   // the batch in flight took the small path
+    // a batch's (kind, R) groups after the first run on these streams, forked
+    // from and joined back into `stream` with events
+    cudaStream_t aux[3] = {};
+    cudaEvent_t forked = nullptr, joined[3] = {};
+};
+
+constexpr int kAuxStreams = 3;
+
+// The stream of a batch's group gi: the slot's own for the first, then the
+// auxiliary streams in turn.  With an upload, fork() records `forked` right
+// after it (before any group is launched) and the first use of an auxiliary
+// stream in the batch waits for it; a small batch has nothing to wait for.
+struct GroupStreams {
+    Slot &sl;
+    bool forked = false;
+    bool used[kAuxStreams] = {};
+    cudaError_t fork()
+    {
+        forked = true;
+        return cudaEventRecord(sl.forked, sl.stream);
+    }
+    cudaStream_t get(int gi, cudaError_t *e)
+    {
+        *e = cudaSuccess;
+        if (gi == 0) return sl.stream;
+        const int a = (gi - 1) % kAuxStreams;
+        if (!used[a]) {
+            if (forked) *e = cudaStreamWaitEvent(sl.aux[a], sl.forked, 0);
+            used[a] = true;
+        }
+        return sl.aux[a];
+    }
+    // the slot's stream waits for every auxiliary stream this batch used
+    cudaError_t join()
+    {
+        cudaError_t e = cudaSuccess;
+        for (int a = 0; a < kAuxStreams && e == cudaSuccess; ++a)
+            if (used[a] && (e = cudaEventRecord(sl.joined[a], sl.aux[a])) == cudaSuccess)
+                e = cudaStreamWaitEvent(sl.stream, sl.joined[a], 0);
+        return e;
+    }
 };
 
 constexpr size_t kSmallCntBytes = 2 * ftv::kSmallTasks * sizeof(unsigned long long);
@@ -209,7 +250,8 @@ int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int til
         return std::make_pair(args[x].kind, args[x].R) < std::make_pair(args[y].kind, args[y].R);
     });
     ftv::SmallGroup g;
-    int gi = 0;
+    GroupStreams gs{sl};
+    int gi = 0, launched = 0;
     for (int i = 0; i < n; ++gi) {
         std::memset(&g, 0, sizeof g);
         g.kind = args[order[i]].kind;
@@ -231,12 +273,15 @@ int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int til
             for (int t = 0; t < g.ntasks; ++t) sl.host_stats[g.tasks[t].stats - sl.small_stats] = initial_stats();
             continue;
         }
-        const int rc = ftv::launch_small_group(g, sl.stream, max_ctas);
+        cudaStream_t st = gs.get(launched++, &e);
+        const int rc = e == cudaSuccess ? ftv::launch_small_group(g, st, max_ctas) : ftv::cuda_fail(e);
         if (rc != FT_OK) {
             sl.small_dirty = true;
+            gs.join();
             return rc;
         }
     }
+    if ((e = gs.join()) != cudaSuccess) return ftv::cuda_fail(e);
     return FT_OK;
 }
 
@@ -291,7 +336,20 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     }
     cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return ftv::cuda_fail(e);
-    if ((rc = ftv::launch_groups(sl.gd, 0, sl.stream, max_ctas)) != FT_OK) return rc;
+    GroupStreams gs{sl};
+    int launched = 0, with_tiles = 0;
+    for (const ftv::GroupDev &g : sl.gd) with_tiles += g.total_tiles > 0;
+    if (with_tiles > 1 && (e = gs.fork()) != cudaSuccess) return ftv::cuda_fail(e);
+    for (const ftv::GroupDev &g : sl.gd) {
+        if (g.total_tiles == 0) continue;
+        cudaStream_t st = gs.get(launched++, &e);
+        rc = e == cudaSuccess ? ftv::launch_group(g, 0, st, max_ctas) : ftv::cuda_fail(e);
+        if (rc != FT_OK) {
+            gs.join();
+            return rc;
+        }
+    }
+    if ((e = gs.join()) != cudaSuccess) return ftv::cuda_fail(e);
     if (any_user) {
         if ((e = cudaMemcpyAsync(sl.dev_user, sl.host_user, sizeof(ft_stats *) * n, cudaMemcpyHostToDevice,
                                  sl.stream)) != cudaSuccess)
@@ -407,6 +465,14 @@ void free_server(ft_server *s)
         if (sl.dev_user) cudaFree(sl.dev_user);
         if (sl.host_user) cudaFreeHost(sl.host_user);
         if (sl.small_area) cudaFree(sl.small_area);
+        for (int a = 0; a < kAuxStreams; ++a) {
+            if (sl.aux[a]) {
+                cudaStreamSynchronize(sl.aux[a]);
+                cudaStreamDestroy(sl.aux[a]);
+            }
+            if (sl.joined[a]) cudaEventDestroy(sl.joined[a]);
+        }
+        if (sl.forked) cudaEventDestroy(sl.forked);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     delete s;
@@ -442,7 +508,15 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
                          sizeof(ft_stats) * (size_t)std::min(cfg->max_slots, 4096);
     for (auto &sl : s->slots) {
         if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess) {
+            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&sl.forked, cudaEventDisableTiming)) != cudaSuccess) {
+            rc = ftv::cuda_fail(e);
+            break;
+        }
+        for (int a = 0; a < kAuxStreams && e == cudaSuccess; ++a)
+            if ((e = cudaStreamCreateWithFlags(&sl.aux[a], cudaStreamNonBlocking)) == cudaSuccess)
+                e = cudaEventCreateWithFlags(&sl.joined[a], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
             rc = ftv::cuda_fail(e);
             break;
         }
