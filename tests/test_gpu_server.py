@@ -376,3 +376,54 @@ def test_empty_requests_and_groups_in_a_batch(user_stats):
             assert info.batches == rnd + 1
     finally:
         fv.ft_server_destroy(srv)
+
+
+@pytest.mark.parametrize("user_stats", [False, True])
+def test_every_kind_and_r_through_the_server(user_stats):
+    """Every element type with every R from 2 to 8 (49 requests with specials,
+    ties and flips, sizes from 1 element to ragged multi-block), voted by a
+    server that packs up to 16 requests per batch, so that batches hold
+    several (kind, R) groups on the auxiliary streams.  Without caller
+    statistics pointers the batches take the small-batch path (each group in
+    a kernel parameter); with them, the upload path.  Voted values, digests
+    and statistics equal the oracle's bit for bit."""
+    from paper_1405_2912_b300 import ftvote as fv
+    from test_gpu_vote import _random_problem
+    dts = ["f32", "f64", "i32", "u32", "i64", "u64", "u8"]
+    sizes = [1, 1023, 4097, 12345, 65536 + 77]
+    probs = []
+    for i, (dt, R) in enumerate((d, r) for d in dts for r in range(2, 9)):
+        reps, tol = _random_problem(dt, R, sizes[i % len(sizes)], seed=7000 + i)
+        probs.append(synth.Problem(reps, dt, *tol))
+    tasks = [DevTask(p) for p in probs]
+    srv = _server(budget=1 << 34, max_slots=16, streams=3, tile=0)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tickets = []
+        for t in tasks:
+            d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+            if not user_stats:
+                d.stats = None
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)) == fv.FT_OK
+            tickets.append(tk.value)
+        fv.ft_server_pause(srv, 0)
+        for p, t, tk in zip(probs, tasks, tickets):
+            r = fv.ft_result()
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+            assert r.status == fv.FT_OK
+            ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+            got = t.result()
+            assert got["out"].tobytes() == ref["out"].tobytes(), (p.dtype, p.R, p.n)
+            assert np.array_equal(got["block_crc"], ref["block_crc"]), (p.dtype, p.R, p.n)
+            views = [_stats_dict(r.stats, p.R)] + ([got] if user_stats else [])
+            for v in views:
+                assert [int(x) for x in v["mismatch"]] == [int(x) for x in ref["mismatch"]], (p.dtype, p.R)
+                assert [int(x) for x in v["first_mismatch"]] == [int(x) for x in ref["first_mismatch"]]
+                assert int(v["no_majority"]) == int(ref["no_majority"])
+                assert int(v["first_no_majority"]) == int(ref["first_no_majority"])
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        assert info.batches >= 4      # 49 requests, at most 16 per batch
+    finally:
+        fv.ft_server_destroy(srv)
