@@ -575,7 +575,15 @@ def run_next_rows(args, dev):
     rating (Sec. IV.B, V.C): the seeded simulation of the paper's injection
     experiment (rating_sim): mean time per result of the fault-aware choice
     and of avoiding the faulty unit after its first fault, across fault
-    probabilities."""
+    probabilities.
+
+    hetdmr (Sec. IV.D, heterogeneous DMR): the task's GPU result resident on
+    the device and its CPU result in pinned host memory (here the GPU result
+    with 1-ULP differences on 10 % of the elements, standing in for CPU
+    rounding), voted by ft_vote_host with the voted buffer and digests left on
+    the device: only the host result crosses PCIe.  Against uploading the
+    host result and then calling ft_vote.  Wall time of the synchronous
+    calls, median of 10."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     out = {}
@@ -675,7 +683,46 @@ def run_next_rows(args, dev):
     out["dmr"] = {"workload": "y = 1.0009765625 * x + 0.1 on 2^26 f32 (two GPU kernels per run), R = 2, rel_tol 1e-3",
                   "single_ms": round(single, 3), "dmr_ms": round(dmr, 3), "overhead": round(dmr / single, 2),
                   "mismatch": s["mismatch"], "paper_overhead_range": "x1 to x3 (Sec. V.B)"}
-    del x, reps, yv, crc
+    # ---- heterogeneous DMR: one result on the device, one in host memory
+    n_h = n
+    gpu_y = reps[0]
+    cpu_np = gpu_y.cpu().numpy().copy()
+    idx = np.flatnonzero(np.random.default_rng(11).random(n_h) < 0.1)
+    synth.ulp_perturb(cpu_np, idx, np.ones(idx.size, dtype=np.int64))
+    cpu_y = torch.from_numpy(cpu_np).pin_memory()
+    hst = fv.ft_stats()
+    dh = fv.make_desc([gpu_y, cpu_y], yv, crc, None, 0.0, fv.FT_PAPER_F32_REL_TOL, dtype="f32", n=n_h)
+    dh.stats = ctypes.addressof(hst)
+    staged = torch.empty_like(gpu_y)
+    dd = fv.make_desc([gpu_y, staged], yv, crc, st, 0.0, fv.FT_PAPER_F32_REL_TOL, dtype="f32", n=n_h)
+
+    def wall_ms(fn, k=10):
+        ts = []
+        for _ in range(2):
+            fn()
+        for _ in range(k):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(ts)
+
+    def upload_then_vote():
+        staged.copy_(cpu_y, non_blocking=True)
+        fv.check(fv.ft_vote(ctypes.byref(dd), fv.stream_handle()), "ft_vote")
+
+    het = wall_ms(lambda: fv.check(fv.ft_vote_host(ctypes.byref(dh), 0), "ft_vote_host"))
+    seq = wall_ms(upload_then_vote)
+    hs = fv.parse_stats(st, 2)
+    out["hetdmr"] = {"workload": "R = 2 f32, 2^26 elements: GPU result on the device, CPU result (1-ULP "
+                                 "differences on 10 %) in pinned host memory, rel_tol 1e-3; voted buffer and "
+                                 "digests left on the device",
+                     "ft_vote_host_ms": round(het, 3), "upload_then_ft_vote_ms": round(seq, 3),
+                     "voter_gb_per_s": round(3 * 4 * n_h / het / 1e6, 1),
+                     "h2d_bytes": 4 * n_h, "mismatch": [int(hst.mismatch[0]), int(hst.mismatch[1])],
+                     "same_as_device_vote": [int(hst.mismatch[r]) for r in range(2)] == hs["mismatch"]}
+    del x, reps, yv, crc, cpu_y, staged
     torch.cuda.empty_cache()
     return out
 
