@@ -220,7 +220,8 @@ typedef struct ft_server_config {
     int32_t  streams;           /* batches in flight at once (1..8)               */
     int32_t  tile_blocks;       /* batched-kernel tile, 1..64; 0 = automatic per batch:
                                    8, halved while the batch would make fewer tiles
-                                   than the kernel has warps in one wave, down to 1 */
+                                   than its share of one wave of the kernel's warps
+                                   (the wave divided by `streams`), down to 1 */
     int32_t  max_inflight;      /* most admitted, not yet collected requests (0 = 65536) */
     uint64_t max_batch_bytes;   /* a batch takes waiting requests (oldest first) while their
                                    (R+1)*n*sizeof(dtype) bytes stay within this, and at least
@@ -238,8 +239,11 @@ typedef struct ft_result {
 } ft_result;
 
 /* Start a server: one host thread that packs admitted requests into batches
- * and launches them on `streams` CUDA streams of the current device.
- * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
+ * and launches them on `streams` CUDA streams of the current device (each
+ * with up to three auxiliary streams, on which a batch's further element-type
+ * / R groups run in parallel).  With two or more streams no batch's kernels
+ * occupy more than all but 16 SMs, so that a batch is not held behind all of
+ * a large one.  Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
 int ft_server_create(ft_server **srv, const ft_server_config *cfg);
 
 /* Admit one request (the replicas must already hold the duplicated results).
