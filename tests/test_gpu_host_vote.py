@@ -103,7 +103,8 @@ def test_empty_and_bad_chunk():
 
 def _mixed_vote(reps, dtype, tol, chunk, where):
     """ft_vote_host with each buffer placed as `where` says: a dict of
-    'rep0'..'repR-1', 'out', 'crc', 'stats' -> 'dev' | 'pinned' | 'pageable'."""
+    'rep0'..'repR-1', 'out', 'crc', 'stats' -> 'dev' | 'pinned' | 'pageable'
+    ('crc' may also be None: no digests)."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     n = reps[0].size
@@ -126,21 +127,21 @@ def _mixed_vote(reps, dtype, tol, chunk, where):
         keep.append(t)
         rp.append(t.data_ptr())
     out = place(np.zeros(max(nb, 16), dtype=np.uint8), where["out"])
-    crc = place(np.zeros(4 * nblk, dtype=np.uint8), where["crc"])
+    crc = place(np.zeros(4 * nblk, dtype=np.uint8), where["crc"]) if where["crc"] else None
     st = place(np.zeros(ctypes.sizeof(fv.ft_stats), dtype=np.uint8), where["stats"])
-    keep += [out, crc, st]
+    keep += [out, st] + ([crc] if crc is not None else [])
     torch.cuda.synchronize()                        # device inputs complete before the call
     d = fv.ft_vote_desc()
     for r, p in enumerate(rp):
         d.replicas[r] = p
     d.R, d.dtype, d.n = len(reps), fv.DTYPE[dtype], n
     d.abs_tol, d.rel_tol = tol
-    d.out, d.block_crc, d.stats = out.data_ptr(), crc.data_ptr(), st.data_ptr()
+    d.out, d.block_crc, d.stats = out.data_ptr(), (crc.data_ptr() if crc is not None else None), st.data_ptr()
     fv.check(fv.ft_vote_host(ctypes.byref(d), chunk), "ft_vote_host")
     s = fv.ft_stats.from_buffer_copy(st.cpu().numpy().tobytes())
     R = len(reps)
     return {"out": out.cpu().numpy()[:nb].view(np_t).copy(),
-            "block_crc": crc.cpu().numpy().view(np.uint32)[:fv.n_blocks(nb)].copy(),
+            "block_crc": (crc.cpu().numpy().view(np.uint32)[:fv.n_blocks(nb)].copy() if crc is not None else None),
             "mismatch": list(s.mismatch)[:R], "first_mismatch": list(s.first_mismatch)[:R],
             "no_majority": s.no_majority, "first_no_majority": s.first_no_majority}
 
@@ -152,6 +153,8 @@ def _mixed_vote(reps, dtype, tol, chunk, where):
     {"rep0": "dev", "rep1": "dev", "rep2": "dev", "out": "pinned", "crc": "dev", "stats": "pageable"},
     # host replicas, device outputs
     {"rep0": "pinned", "rep1": "pinned", "rep2": "pinned", "out": "dev", "crc": "dev", "stats": "pinned"},
+    # no digests, the output on the host
+    {"rep0": "dev", "rep1": "pageable", "rep2": "dev", "out": "pageable", "crc": None, "stats": "dev"},
 ])
 def test_mixed_residency(where):
     rng = np.random.default_rng(11)
@@ -163,7 +166,10 @@ def test_mixed_residency(where):
         synth.bit_flip(reps[r], idx, rng.integers(0, 32, size=idx.size))
     tol = synth.TOL["f32"]
     ref = oracle.vote(reps, "f32", *tol)
-    _check(_mixed_vote(reps, "f32", tol, 2 * 8192, where), ref)
+    got = _mixed_vote(reps, "f32", tol, 2 * 8192, where)
+    if where["crc"] is None:
+        got["block_crc"] = ref["block_crc"]       # none asked for
+    _check(got, ref)
 
 
 def test_mixed_residency_empty_device_stats():
