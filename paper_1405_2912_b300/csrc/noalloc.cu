@@ -204,9 +204,18 @@ static int vote_batched_noalloc(const ft_vote_desc *descs, int ntasks, int tile_
         const int rc = validate_desc(&descs[i]);
         if (rc != FT_OK) return rc;
     }
+    // The batch reaches the device through copies from one static host
+    // staging area that every call refills.  Recorded into a graph, such a
+    // copy would read that area when the graph is replayed, by which time a
+    // later call may have refilled it with another batch; so a stream that is
+    // being captured is refused.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cap != cudaStreamCaptureStatusNone) return FT_EINVAL;
     if (ntasks == 0) return FT_OK;
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
     if (dev < 0 || dev >= kMaxDevices) return FT_EINVAL;
     unsigned char *scratch = nullptr;
