@@ -2,16 +2,17 @@
 element count beyond 2^32 (64-bit indices).
 
 - batched, 4096 tasks (43 GB of replicas and outputs), in the launch
-  configuration bench.py times: every task equals its own ft_vote bit for bit,
-  and sampled tasks equal the oracle;
+  configuration bench.py times: every task equals the oracle's vote of its
+  replicas and its own ft_vote, bit for bit;
 - serving, the 20 000 req/s Poisson stream over 64 resident payloads: every
-  request reports the statistics of its payload voted alone, and sampled
-  payloads equal the oracle;
+  payload voted alone equals the oracle, and every request reports the
+  statistics of its payload voted alone;
 - a u8 vote of n = 2^32 + 4113 elements with faults planted above 2^32: counts,
   64-bit first indices and the digests of the blocks around the faults follow
   from the construction (and, for the digests, from the oracle's CRC of those
   blocks)."""
 import collections
+import concurrent.futures as cf
 import ctypes
 
 import numpy as np
@@ -25,17 +26,28 @@ from _gpu import DevTask, assert_same, desc_array
 pytestmark = pytest.mark.gpu
 
 
+def _check_all_against_oracle(probs_of, tasks, threads=None):
+    """Every task's device result against the oracle's vote of its replicas,
+    regenerated from the seeded generator (probs_of(i)) in a thread pool so
+    that only a few tasks' host replicas exist at a time."""
+    import os
+    threads = threads or max(2, min(32, len(os.sched_getaffinity(0))))
+
+    def one(i):
+        p = probs_of(i)
+        assert_same(tasks[i].result(), oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
+        return i
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        done = list(ex.map(one, range(len(tasks))))
+    assert done == list(range(len(tasks)))
+
+
 def test_batched_full_size():
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     specs = synth.cfg4_specs()
-    tasks, probs_sampled = [], {}
-    sample = set(range(0, len(specs), 171)) | {int(np.argmax([s.n for s in specs]))}
-    for i, s in enumerate(specs):
-        p = synth.task_problem(s)
-        tasks.append(DevTask(p))
-        if i in sample:
-            probs_sampled[i] = p
+    tasks = [DevTask(synth.task_problem(s)) for s in specs]
     plan = ctypes.c_void_p()
     fv.check(fv.ft_plan_create(ctypes.byref(plan), desc_array(tasks), len(tasks), None), "ft_plan_create")
     try:
@@ -46,13 +58,13 @@ def test_batched_full_size():
             got.append((t.out[:t.nbytes].clone(), t.crc[:t.nb].clone(), t.stats.clone()))
     finally:
         fv.ft_plan_destroy(plan)
+    # every task against the oracle (the batched results are still in place)
+    _check_all_against_oracle(lambda i: synth.task_problem(specs[i]), tasks)
     for t in tasks:
         fv.check(fv.ft_vote(ctypes.byref(t.desc), fv.stream_handle()), "ft_vote")
     torch.cuda.synchronize()
     for i, (t, (o, c, s)) in enumerate(zip(tasks, got)):
         assert torch.equal(o, t.out[:t.nbytes]) and torch.equal(c, t.crc[:t.nb]) and torch.equal(s, t.stats), i
-    for i, p in probs_sampled.items():
-        assert_same(tasks[i].result(), oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
 
 
 def test_serving_full_stream():
@@ -66,9 +78,7 @@ def test_serving_full_stream():
         fv.check(fv.ft_vote(ctypes.byref(t.desc), fv.stream_handle()), "ft_vote")
     torch.cuda.synchronize()
     alone = [t.result() for t in tasks]
-    for i in range(0, len(probs), 9):
-        p = probs[i]
-        assert_same(alone[i], oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
+    _check_all_against_oracle(lambda i: probs[i], tasks)
     descs = []
     for t in tasks:
         d = fv.ft_vote_desc.from_buffer_copy(t.desc)
