@@ -61,6 +61,7 @@ def make_problem(args):
 
 
 FALLBACK_HBM_GBS = 6400.0
+L2_BYTES = 126 << 20
 
 
 KERNEL_SOURCES = ("paper_1405_2912_b300/csrc/common.cuh", "paper_1405_2912_b300/csrc/vote.cu")
@@ -229,8 +230,9 @@ def host_cores() -> int:
 
 def config_of(problem, ws, workload):
     nb = problem.bytes_moved
-    l2 = (f"inputs ({nb / 2**30:.2f} GiB per step) exceed the 126 MB L2; no flush" if nb > (126 << 20)
-          else f"inputs ({nb / 2**20:.0f} MiB per step) fit in L2")
+    l2 = (f"inputs ({nb / 2**30:.2f} GiB per step) exceed the 126 MB L2; no flush" if nb > L2_BYTES
+          else f"inputs ({nb / 2**20:.0f} MiB per step) fit in L2: a 504 MiB buffer is written before each "
+               "timed vote (L2 flushed) and each vote is timed alone between two CUDA events")
     return {"workload": WORKLOADS[workload], "R": problem.R, "n": problem.n, "bytes_per_step": nb, "l2": l2,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
 
@@ -280,6 +282,8 @@ def run_ours(args, problem, ws, rank, local):
     stats = fv.new_stats(dev)
     desc = fv.make_desc(reps, out, crc, stats, problem.abs_tol, problem.rel_tol, dtype=problem.dtype, n=n)
     pd = ctypes.byref(desc)
+    flush_l2 = problem.bytes_moved <= L2_BYTES
+    scrub = torch.empty(4 * L2_BYTES, dtype=torch.uint8, device=dev) if flush_l2 else None
     torch.cuda.synchronize()
 
     ev_start, ev_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -289,16 +293,41 @@ def run_ours(args, problem, ws, rank, local):
     launches0 = fv.ft_launch_count()
     barrier(ws)
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        ev_start.record(stream)
-        for k in range(args.steps):
-            fv.ft_vote(pd, sh)
-        ev_end.record(stream)
-    torch.cuda.synchronize()
+    warm_l2_us = None
+    if flush_l2:
+        # inputs that fit in L2: each timed vote follows a write of a buffer
+        # four times the L2's size, so that it reads its replicas and tables
+        # from HBM, and is timed alone between two events
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                scrub.fill_(k & 0xFF)
+                pairs[k][0].record(stream)
+                fv.ft_vote(pd, sh)
+                pairs[k][1].record(stream)
+        torch.cuda.synchronize()
+        elapsed = sum(a.elapsed_time(b) for a, b in pairs) / 1e3
+    else:
+        with torch.cuda.stream(stream):
+            ev_start.record(stream)
+            for k in range(args.steps):
+                fv.ft_vote(pd, sh)
+            ev_end.record(stream)
+        torch.cuda.synchronize()
+        elapsed = ev_start.elapsed_time(ev_end) / 1e3                  # s, whole timed region
     barrier(ws)
     launches = fv.ft_launch_count() - launches0
     clocks = sampler.stop()
-    elapsed = ev_start.elapsed_time(ev_end) / 1e3                      # s, whole timed region
+    if flush_l2:
+        # the same votes back to back with everything resident in L2, for context
+        with torch.cuda.stream(stream):
+            ev_start.record(stream)
+            for k in range(args.steps):
+                fv.ft_vote(pd, sh)
+            ev_end.record(stream)
+        torch.cuda.synchronize()
+        warm_l2_us = round(ev_start.elapsed_time(ev_end) * 1e3 / args.steps, 2)
     t_max = max_over_ranks(elapsed, ws)
     bytes_step = problem.bytes_moved
     value = bytes_step * args.steps * ws / t_max / 1e9
@@ -375,7 +404,7 @@ def run_ours(args, problem, ws, rank, local):
         t_d = d0.elapsed_time(d1) / 1e3 / args.digest_reps
         digest = {"bytes_per_call": nbytes, "gb_per_s": round(nbytes / t_d / 1e9, 1),
                   "us_per_call": round(t_d * 1e6, 1), "matches_fused_digest": bool(torch.equal(dout, crc))}
-    del reps, out, crc
+    del reps, out, crc, scrub
     # the batched and serving forms are measured on a single-rank run (each is a
     # whole-GPU workload of its own; a scaling run times the vote step only)
     batched = run_batched(args, dev, stream) if args.batched_tasks > 0 and ws == 1 else None
@@ -391,7 +420,15 @@ def run_ours(args, problem, ws, rank, local):
         dt, b = oracle_run(problem, n_s, cores)
         cpu = {"value": round(b / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"first {n_s} of {n} elements, 4 KiB-aligned chunks on {cores} threads, one pass"}
+    # The detailed sections come first and the compact summaries of the
+    # batched and serving forms last, so that the end of the line (what a
+    # tail of the output shows) carries all three parts of the metric.
     line = {
+        "size_sweep": size_sweep,
+        "next_rows": next_rows,
+        "digest": digest,
+        "batched_detail": batched,
+        "serving_detail": serving,
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
         "ms_per_step": round(1e3 * t_max / args.steps, 4),
@@ -399,6 +436,8 @@ def run_ours(args, problem, ws, rank, local):
         "data": "synthetic",
         "config": config_of(problem, ws, args.workload),
         "hbm_frac_of_8tbs_spec": round(value / ws / 8000.0, 4),
+        "us_per_vote": round(1e6 * t_max / args.steps, 2),
+        "us_per_vote_warm_l2_back_to_back": warm_l2_us,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "traffic": args.traffic if args.traffic is not None else (
@@ -410,13 +449,45 @@ def run_ours(args, problem, ws, rank, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "result": {"mismatch": s["mismatch"], "no_majority": s["no_majority"]},
-        "digest": digest,
-        "batched": batched,
-        "serving": serving,
-        "size_sweep": size_sweep,
-        "next_rows": next_rows,
+        "digest_gb_per_s": digest["gb_per_s"] if digest else None,
+        "batched": batched_summary(batched),
+        "serving": serving_summary(serving),
     }
     print(json.dumps(line), flush=True)
+
+
+def batched_summary(b):
+    """The batched figures that the end of the JSON line carries."""
+    if not b:
+        return None
+    out = {"tasks": b["tasks"], "tasks_per_s": b["tasks_per_s"], "gb_per_s": b["gb_per_s"],
+           "per_task_launches_tasks_per_s": b["per_task_launches"]["tasks_per_s"],
+           "speedup_vs_per_task": b["speedup_vs_per_task"],
+           "noalloc_tasks_per_s": b["noalloc"]["tasks_per_s"] if b.get("noalloc") else None,
+           "launches_per_batch": b["launches_per_batch"], "tune": b["tune"]}
+    return out
+
+
+def serving_summary(sv):
+    """p50 / p99 latency and throughput of each serving arm at each rate."""
+    if not sv:
+        return None
+    out = {}
+    for rate_key in ("at_20k_req_per_s", "at_60k_req_per_s"):
+        r = sv.get(rate_key)
+        if not r:
+            continue
+        arms = {}
+        for arm in ("continuous_batching", "unbatched", "plain_ft_vote"):
+            a = r.get(arm)
+            if not a:
+                continue
+            arms[arm] = {"p50_us": a["p50_us"], "p99_us": a["p99_us"], "req_per_s": a["req_per_s"]}
+            if "mean_requests_per_batch" in a:
+                arms[arm]["req_per_batch"] = a["mean_requests_per_batch"]
+                arms[arm]["launch_host_us_per_batch"] = a["launch_host_us_per_batch"]
+        out[rate_key] = arms
+    return out
 
 
 def device_tasks(specs, dev, config_id, threads, stats_ptr=True):
@@ -496,6 +567,7 @@ def run_batched(args, dev, stream):
     torch.cuda.empty_cache()
     return {"workload": f"{len(specs)} tasks, n log-uniform [2^10, 2^22], f32/f64/i32 40/30/30 %, R=3, "
                         "one replica with bit flips (1e-4/element) in 5 % of tasks",
+            "tasks": len(specs),
             "tasks_per_s": round(len(specs) / t_b, 1), "gb_per_s": round(nbytes / t_b / 1e9, 1),
             "ms_per_batch": round(t_b * 1e3, 3), "bytes_per_batch": nbytes,
             "launches_per_batch": int(launches_b), "tune": {"tile_blocks": tune.tile_blocks,
@@ -511,13 +583,25 @@ def run_serving(args, dev):
     """Poisson arrivals of votes with n log-uniform 4K..16M, R in {3, 5},
     f32/f64, under a 40 GB budget, replicas resident: continuous batching
     (batches capped at 1 GB of request bytes) against one-request batches on
-    the same 3 streams, at the workload's 20k requests/s and at three times
-    that load."""
+    the same 3 streams, and against plain ft_vote calls issued at each arrival
+    on 3 streams in turn (no server), at the workload's 20k requests/s and at
+    three times that load."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     from paper_1405_2912_b300 import serving
     _, specs = synth.cfg5_requests(duration_s=args.serve_seconds, rate=args.serve_rate, pool=args.serve_pool)
     keep, descs, _, _ = device_tasks(specs, dev, 5, host_cores(), stats_ptr=False)
+    # per-stream copies of the descriptors with statistics buffers, for the
+    # plain per-request arm (ft_vote needs them; the server keeps its own)
+    plain_stats = torch.empty((3, len(specs), 18), dtype=torch.int64, device=dev)
+    plain_descs = []
+    for si in range(3):
+        row = []
+        for p in range(len(specs)):
+            d = fv.ft_vote_desc.from_buffer_copy(descs[p])
+            d.stats = plain_stats[si, p].data_ptr()
+            row.append(d)
+        plain_descs.append(row)
     torch.cuda.synchronize()
     out = {"workload": f"Poisson arrivals for {args.serve_seconds} s, n log-uniform [2^12, 2^24], R in {{3,5}}, "
                        f"f32/f64 50/50, 40 GB budget, {len(specs)} resident payloads, 3 streams",
@@ -528,6 +612,11 @@ def run_serving(args, dev):
         payload = np.array([r.payload for r in reqs])
         per_req = np.array([(specs[r.payload].R + 1) * r.n * (4 if r.dtype == "f32" else 8) for r in reqs])
         res = {"offered_gb_per_s": round(float(per_req.sum()) / args.serve_seconds / 1e9, 1)}
+        # the plain arm: one ft_vote per request on 3 streams in turn, no server
+        warm = min(len(reqs), 300)
+        serving.replay_plain(plain_descs, arrivals[:warm] - arrivals[0], payload[:warm])
+        r = serving.replay_plain(plain_descs, arrivals, payload)
+        res["plain_ft_vote"] = serving.summarize(r, per_req)
         for name, slots, cap in (("continuous_batching", 4096, 1 << 30), ("unbatched", 1, 0)):
             cfg = fv.ft_server_config(int(40e9), slots, 3, 0, 0, cap)
             srv = ctypes.c_void_p()
@@ -553,7 +642,7 @@ def run_serving(args, dev):
                                                                 / max(1, nb), 1),
                               "batch_span_us_mean": round((info.batch_span_us - info0.batch_span_us) / max(1, nb), 1)})
         out[label] = res
-    del keep
+    del keep, plain_stats
     torch.cuda.empty_cache()
     return out
 

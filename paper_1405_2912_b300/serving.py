@@ -94,3 +94,60 @@ def summarize(r, bytes_per_req):
             "req_per_s": round(n / r["span_s"], 1) if r["span_s"] > 0 else None,
             "gb_per_s": round(float(np.sum(bytes_per_req)) / r["span_s"] / 1e9, 2) if r["span_s"] > 0 else None,
             "budget_refusals": int(r["refused"]), "errors": int(r["errors"])}
+
+
+def replay_plain(descs, arrivals_s, payload_of, nstreams=3, start_delay_us=2000.0):
+    """The same arrival stream without a server: each request is one ft_vote
+    call, issued at its arrival on the next of `nstreams` streams in turn,
+    followed by an event on that stream.  The loop that issues the calls also
+    polls the oldest outstanding event of each stream and takes the time at
+    which it sees it complete, as the server's worker does for a batch, so
+    that latency = seen complete - scheduled arrival has the same meaning in
+    both.  descs[s][p] is payload p's descriptor for stream s (each stream
+    with its own statistics buffers, so that two requests in flight on
+    different streams never share one)."""
+    was_enabled = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        return _replay_plain(descs, arrivals_s, payload_of, nstreams, start_delay_us)
+    finally:
+        if was_enabled:
+            gc.enable()
+
+
+def _replay_plain(descs, arrivals_s, payload_of, nstreams, start_delay_us):
+    import torch
+    n = len(arrivals_s)
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    handles = [int(s.cuda_stream) for s in streams]
+    events = [torch.cuda.Event() for _ in range(max(n, 1))]
+    refs = [[ctypes.byref(d) for d in per_stream] for per_stream in descs]
+    vote, clock = fv.ft_vote, fv.ft_clock_us
+    queues = [collections.deque() for _ in range(nstreams)]
+    done_at = np.zeros(n, dtype=np.float64)
+    issued_at = np.zeros(n, dtype=np.float64)
+    errors = 0
+    torch.cuda.synchronize()
+    t0 = clock() + start_delay_us
+    arr = t0 + np.asarray(arrivals_s, dtype=np.float64) * 1e6
+    i = head = 0
+    while head < n:
+        now = clock()
+        while i < n and arr[i] <= now:
+            s = i % nstreams
+            issued_at[i] = clock()
+            if vote(refs[s][payload_of[i]], handles[s]) != fv.FT_OK:
+                errors += 1
+            events[i].record(streams[s])
+            queues[s].append(i)
+            i += 1
+        for q in queues:
+            while q and events[q[0]].query():
+                done_at[q.popleft()] = clock()
+                head += 1
+    torch.cuda.synchronize()
+    lat = done_at - arr
+    span_s = (done_at.max() - arr.min()) / 1e6 if n else 0.0
+    return {"latency_us": lat, "submit_lag_us": issued_at - arr, "server_us": done_at - issued_at,
+            "refused": 0, "span_s": span_s, "errors": errors}
