@@ -108,9 +108,17 @@ typedef struct ft_vote_desc {
     ft_stats   *stats;
 } ft_vote_desc;
 
-/* Vote one task (Sec. IV.D).  Two launches on `stream`: a statistics reset and
- * the persistent voter kernel (128-bit coalesced loads of all R replicas,
- * vote, store, warp-ballot statistics and the fused per-block CRC32C).
+/* Vote one task (Sec. IV.D) with the persistent voter kernel (128-bit
+ * coalesced loads of all R replicas, vote, store, warp-ballot statistics and
+ * the fused per-block CRC32C).  Normally one launch on `stream`: the
+ * statistics are gathered in a library-owned slot (a pool per device, created
+ * by the first call on it) and copied to desc->stats by the kernel's last CTA.
+ * While `stream` is being captured into a graph, or when every slot is in use,
+ * a statistics reset kernel runs first and the voter adds into desc->stats
+ * directly.  The voter lets the next kernel on the stream start early under
+ * programmatic dependent launch: a kernel launched after ft_vote with
+ * programmatic stream serialization must call cudaGridDependencySynchronize()
+ * before it reads the vote's results.
  * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
 int ft_vote(const ft_vote_desc *desc, ft_stream stream);
 
@@ -199,11 +207,14 @@ int ft_plan_destroy(ft_plan *plan);
  *                halved while the batch would make fewer tiles than the
  *                kernel has warps in one wave, down to 1.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
- * share the array and it keeps the last call's contents (counters and
- * statistics are reset at the start of each call): calls whose work overlaps
- * on the GPU race on it, so order them on one stream or synchronise between
- * them.  Host threads are serialised while a call builds its batch.
+ * device current).  The batch is copied to the array from a static host area
+ * that every call refills, so a call on a stream that is being captured into
+ * a graph is refused with FT_EINVAL (a replay would copy whatever batch the
+ * area holds by then).  All calls share the array and it keeps the last
+ * call's contents (counters and statistics are reset at the start of each
+ * call): calls whose work overlaps on the GPU race on it, so order them on one
+ * stream or synchronise between them.  Host threads are serialised while a
+ * call builds its batch.
  * Returns FT_OK, FT_EINVAL or FT_ECUDA. */
 #define FT_NOALLOC_MAX_TASKS 4096
 int ft_vote_batched_noalloc(const ft_vote_desc *tasks, int32_t ntasks, int32_t tile_blocks,

@@ -834,14 +834,14 @@ __device__ __forceinline__ const uint8_t *rep_for_lane(const TaskArgs &a, int la
 // measured 9 % slower on 3 x 256M f32: the table lookups then sit between the
 // vote and the next loads.
 // ---------------------------------------------------------------------------
-template <int K, int R>
+template <int K, int R, int JB = kSubBatch<K, R>>
 __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long long b, unsigned long long b_next,
                                                 const uint32_t *s_crc, const CrcLane &L, LaneStats<R> &st, int lane)
 {
     using E = Elem<K>;
     using V = typename E::V;
     constexpr int kPerVec = 16 / E::kSize;
-    constexpr int JB = kSubBatch<K, R>;                      // vectors per lane per sub-batch
+    static_assert(JB == 1 || JB == 2 || JB == 4 || JB == 8, "JB: vectors per lane per sub-batch");
     constexpr unsigned long long kEpb = kBlockBytes / E::kSize;
     constexpr Form F = kForm<K, R>;
     static_assert(F == F_BITS || JB * kPerVec <= 64, "`flagged` holds one bit per element of a sub-batch");

@@ -11,9 +11,13 @@ namespace ftv {
 
 struct TaskArgs;
 
-// Optional launch override of the single-task voter (tests and tuning).
+// Optional launch override of the single-task voter (tests and tuning); zero
+// fields keep the library's choice.
 struct VoteLaunch {
     int ctas_per_sm;   // 0 = occupancy limit
+    int warps;         // warps per CTA (f32 R = 3: 4, 8 or 16; other kinds: the shapes built for them)
+    int sub_batch;     // 16-byte vectors per lane per sub-batch (f32 R = 3: 4 or 8)
+    int stats_mode;    // 1 = statistics reset kernel + voter, 2 = one kernel with a statistics slot
 };
 
 extern std::atomic<unsigned long long> g_launches;
