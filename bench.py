@@ -536,6 +536,13 @@ def run_batched(args, dev, stream):
     plan_s = time.perf_counter() - t0
     tune = fv.ft_tune()
     fv.ft_plan_tune(plan, ctypes.byref(tune))
+    ng = ctypes.c_int32()
+    fv.ft_plan_groups(plan, None, 0, ctypes.byref(ng))
+    garr = (fv.ft_plan_group * max(1, ng.value))()
+    fv.ft_plan_groups(plan, garr, ng.value, ctypes.byref(ng))
+    dname = {v: k for k, v in fv.DTYPE.items()}
+    groups = [{"dtype": dname[g.dtype], "R": g.R, "tasks": g.tasks, "warps": g.warps,
+               "l2_prefetch": bool(g.l2_prefetch)} for g in list(garr)[:ng.value]]
 
     def timed(fn, reps):
         for _ in range(3):
@@ -570,8 +577,10 @@ def run_batched(args, dev, stream):
             "tasks": len(specs),
             "tasks_per_s": round(len(specs) / t_b, 1), "gb_per_s": round(nbytes / t_b / 1e9, 1),
             "ms_per_batch": round(t_b * 1e3, 3), "bytes_per_batch": nbytes,
-            "launches_per_batch": int(launches_b), "tune": {"tile_blocks": tune.tile_blocks,
-                                                            "ctas_per_sm": tune.ctas_per_sm},
+            "launches_per_batch": int(launches_b),
+            "tune": {"tile_blocks": tune.tile_blocks,
+                     "groups": [f"{g['dtype']} R={g['R']}: {g['warps']} warps"
+                                f"{' + L2 prefetch' if g['l2_prefetch'] else ''}" for g in groups]},
             "per_task_launches": {"tasks_per_s": round(len(specs) / t_p, 1), "gb_per_s": round(nbytes / t_p / 1e9, 1),
                                   "ms_per_batch": round(t_p * 1e3, 3)},
             "speedup_vs_per_task": round(t_p / t_b, 2),

@@ -151,22 +151,51 @@ int ft_digest(const void *buf, uint64_t nbytes, uint32_t block_bytes,
 
 /* ---- batched form: many tasks in one persistent, graph-captured launch ---- */
 
-/* Tuning of the batched kernel.  tile_blocks = 4 KiB blocks per work tile
- * (1..64); ctas_per_sm = resident CTAs per SM requested (1..8); 0 = choose by
- * autotuning when the plan is created. */
+/* Tuning of the batched kernels.  A batch is voted by one persistent kernel
+ * per (element kind, R) group; the fields apply to every group, and zeros
+ * leave the choice to the autotuner when the plan is created.
+ *   tile_blocks  4 KiB blocks per work tile (1..64); 0 = autotuned.
+ *   ctas_per_sm  cap on resident CTAs per SM (1..8); 0 = as many as fit.  A
+ *                voter CTA fills an SM's shared memory with its CRC tables,
+ *                so one CTA per SM is what fits, and it is not searched.
+ *   warps        warps per CTA: 8, 12 or 16; 0 = chosen per group.
+ *   l2_prefetch  1 = no prefetch, 2 = each warp prefetches its tile's next
+ *                block into L2; 0 = chosen per group.  When warps or
+ *                l2_prefetch is set, every group takes that shape (warps 0
+ *                then meaning 16, l2_prefetch 0 no prefetch).
+ * ft_plan_tune reports the tile size, and a warps / l2_prefetch value only
+ * when every group has it (0 when the groups differ; ft_plan_groups gives
+ * each group's). */
 typedef struct ft_tune {
     int32_t tile_blocks;
     int32_t ctas_per_sm;
+    int32_t warps;
+    int32_t l2_prefetch;
 } ft_tune;
+
+/* One (element kind, R) group of a plan and the launch shape it runs with. */
+typedef struct ft_plan_group {
+    int32_t  dtype;        /* FT_F32, FT_F64, FT_U8, or for bit-compared integers of
+                              4 / 8 bytes FT_I32 / FT_I64 (the unsigned ones share them) */
+    int32_t  R;
+    int32_t  tasks;        /* tasks in the group */
+    int32_t  warps;        /* warps per CTA of its kernel */
+    int32_t  l2_prefetch;  /* 1 if a warp prefetches its tile's next block into L2 */
+    int32_t  tile_blocks;  /* 4 KiB blocks per work tile */
+    uint64_t tiles;        /* work tiles of the group */
+} ft_plan_group;
 
 typedef struct ft_plan ft_plan;   /* library-owned */
 
 /* Build a plan for ntasks votes (each described as for ft_vote; every task
  * has its own dtype, R, tolerances and outputs; element indices in the
  * statistics are local to the task).  The plan copies the descriptors to a
- * device task table, autotunes the tile size and CTA count when `tune` is NULL
- * or holds zeros (timing real launches on the plan's buffers, which it
- * overwrites), and captures a CUDA graph of the reset + batched kernel.
+ * device task table, autotunes what `tune` leaves open (NULL: everything) by
+ * timing replays of the graph it will capture on the plan's own buffers,
+ * which it overwrites: first the tile size, then each group's warps per CTA
+ * and L2 prefetch in turn; the result is kept per batch signature for later
+ * plans of the process.  It then captures one CUDA graph: the statistics
+ * reset followed by the groups' persistent kernels as parallel branches.
  * The caller keeps every buffer alive and in place until ft_plan_destroy.
  * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
 int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks,
@@ -184,6 +213,10 @@ int ft_vote_many(const ft_vote_desc *descs, int32_t n, ft_stream stream);
 
 /* The tuning the plan uses. */
 int ft_plan_tune(const ft_plan *plan, ft_tune *out);
+
+/* The plan's groups in launch order: out receives min(max, count) entries and
+ * *n the count.  Returns FT_OK or FT_EINVAL. */
+int ft_plan_groups(const ft_plan *plan, ft_plan_group *out, int32_t max, int32_t *n);
 
 /* Free the plan.  Its replays must have completed (synchronize the streams
  * they were launched on first). */

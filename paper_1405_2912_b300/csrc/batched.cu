@@ -1,7 +1,8 @@
 // batched.cu -- the batched voter: thousands of tasks of uneven size and mixed
 // element type voted by persistent kernels that pull work tiles from a device
 // counter, captured together with the statistics reset in one CUDA graph
-// (ft_plan_create / ft_vote_batched), and the tile-size / CTA autotuner.
+// (ft_plan_create / ft_vote_batched), and the autotuner of the tile size and
+// of each group's launch shape.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -18,227 +19,70 @@
 
 namespace ftv {
 
-// Statistics hand-off at the end of a group kernel.  The last CTA to finish
-// copies the statistics of tasks[0..ntasks) to stats_out[tasks[t].stats -
-// stats_base] (host-mapped memory), so that no download follows the kernel.
-// Every thread's statistics atomics are made visible at device scope before
-// its CTA is counted, and the last CTA reads the final values from L2.  With
-// `reset`, it then puts each statistics word back to its initial value and
-// zeroes the tile and done counters, leaving the buffers ready for the next
-// launch without an upload.
-struct CopyOut {
-    unsigned long long *done_ctas;
-    unsigned long long *counter;   // zeroed when reset
-    const TaskArgs *tasks;
-    int ntasks;
-    bool reset;
-    const ft_stats *stats_base;
-    ft_stats *stats_out;
-};
-
-__device__ __noinline__ void copy_out_if_last(const CopyOut &c)
+const void *group_kernel(int kind, int R, int warps, bool pf, bool small)
 {
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(c.done_ctas, 1ull) == (unsigned long long)gridDim.x - 1ull;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    constexpr int kWords = (int)(sizeof(ft_stats) / 8);   // mismatch[8], first[8], no_majority, first
-    static_assert(kWords == 2 * FT_MAX_R + 2, "ft_stats layout");
-    const int n = c.ntasks * kWords;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int w = i % kWords;
-        ft_stats *src = c.tasks[i / kWords].stats;
-        unsigned long long *word = reinterpret_cast<unsigned long long *>(src) + w;
-        reinterpret_cast<unsigned long long *>(c.stats_out + (src - c.stats_base))[w] = __ldcg(word);
-        if (c.reset) *word = (w < FT_MAX_R || w == 2 * FT_MAX_R) ? 0ull : ~0ull;   // counts 0, first indices -1
-    }
-    if (c.reset && threadIdx.x == 0) {
-        *c.counter = 0;
-        *c.done_ctas = 0;
-    }
-    __threadfence_system();
-}
-
-// The task of a tile: from the tile map (plans and large batches) ...
-struct MapLookup {
-    const TaskArgs *tasks;
-    const uint32_t *tile_task;
-    const unsigned long long *tile_first;
-    __device__ __forceinline__ int task_of(unsigned long long tg, int) const { return (int)tile_task[tg]; }
-};
-
-// ... or, for a batch of at most 32 tasks, as the last task whose first tile
-// is at or before it (one ballot; an empty task shares its first tile with
-// the next task, or starts at the group's end, so it is never picked).
-struct ScanLookup {
-    const TaskArgs *tasks;
-    const unsigned long long *tile_first;
-    int ntasks;
-    __device__ __forceinline__ int task_of(unsigned long long tg, int lane) const
-    {
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, lane < ntasks && tile_first[lane] <= tg);
-        return 31 - __clz((int)m);
-    }
-};
-
-// ---------------------------------------------------------------------------
-// K3: persistent batched voter for one (kind, R) group.  A warp claims the
-// next tile with one atomic, looks up its task, votes the tile's 4 KiB blocks
-// (and the task's partial last block when the tile holds it), and flushes its
-// per-task statistics whenever it moves to another task.  Tiles are claimed
-// in increasing order, so a warp meets each task's blocks in increasing order
-// and the first index it sees per replica is its minimum.
-// ---------------------------------------------------------------------------
-template <int K, int R, class Lookup>
-__device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long *counter, unsigned long long total_tiles,
-                                           int tile_blocks, const uint32_t *s_crc)
-{
-    const int lane = threadIdx.x & 31;
-    CrcLane L;
-    L.init(lane);
-    LaneStats<R> st;
-    st.init();
-    int cur = -1;
-    ft_stats *cur_stats = nullptr;
-    for (;;) {
-        unsigned long long tg = 0;
-        if (lane == 0) tg = atomicAdd(counter, 1ull);
-        tg = __shfl_sync(0xFFFFFFFFu, tg, 0);
-        if (tg >= total_tiles) break;
-        const int t = lk.task_of(tg, lane);
-        const TaskArgs a = lk.tasks[t];
-        if (t != cur) {
-            if (cur >= 0) st.flush(cur_stats, lane);
-            st.init();
-            cur = t;
-            cur_stats = a.stats;
-        }
-        const unsigned long long k = tg - lk.tile_first[t];
-        const unsigned long long b0 = k * (unsigned long long)tile_blocks;
-        const unsigned long long b1 = min(b0 + (unsigned long long)tile_blocks, a.nfull);
-        for (unsigned long long b = b0; b < b1; ++b)
-            vote_full_block<K, R>(a, b, ~0ull, s_crc, L, st, lane);
-        if (a.tail_bytes && a.nfull / tile_blocks == k) {
-            LaneStats<R> ts;
-            ts.init();
-            vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
-            st.merge(ts);
-        }
-    }
-    if (cur >= 0) st.flush(cur_stats, lane);
-}
-
-template <int K, int R, int W>
-__global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    load_crc_tables<W>(s_crc);
-    __syncthreads();
-    vote_tiles<K, R>(MapLookup{g.tasks, g.tile_task, g.tile_first}, g.counter, g.total_tiles, g.tile_blocks, s_crc);
-    if (g.done_ctas)
-        copy_out_if_last(CopyOut{g.done_ctas, nullptr, g.tasks + g.t0, g.t1 - g.t0, false, g.stats_base, g.stats_out});
-}
-
-// The same voter for a small batch whose whole group travels in the kernel
-// parameters (no upload); its counters and statistics are left reset for the
-// next launch by the last CTA.
-template <int K, int R, int W>
-__global__ void __launch_bounds__(W * 32, 1) batched_small_kernel(const __grid_constant__ SmallGroup g)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    load_crc_tables<W>(s_crc);
-    __syncthreads();
-    vote_tiles<K, R>(ScanLookup{g.tasks, g.tile_first, g.ntasks}, g.counter, g.total_tiles, g.tile_blocks, s_crc);
-    copy_out_if_last(CopyOut{g.done_ctas, g.counter, g.tasks, g.ntasks, true, g.stats_base, g.stats_out});
-}
-
-template <int K, int R>
-static const void *group_fn(bool small)
-{
-    return small ? reinterpret_cast<const void *>(batched_small_kernel<K, R, kBatchWarps>)
-                 : reinterpret_cast<const void *>(batched_kernel<K, R, kBatchWarps>);
-}
-
-template <int K>
-static const void *group_fn_k(int R, bool small)
-{
-    switch (R) {
-    case 2: return group_fn<K, 2>(small);
-    case 3: return group_fn<K, 3>(small);
-    case 4: return group_fn<K, 4>(small);
-    case 5: return group_fn<K, 5>(small);
-    case 6: return group_fn<K, 6>(small);
-    case 7: return group_fn<K, 7>(small);
-    case 8: return group_fn<K, 8>(small);
+    switch (warps) {
+    case 8: return group_fn_w<8>(kind, R, pf, small);
+    case 12: return group_fn_w<12>(kind, R, pf, small);
+    case 0:
+    case 16: return group_fn_w<16>(kind, R, pf, small);
     default: return nullptr;
     }
 }
 
-static const void *group_kernel(int kind, int R, bool small = false)
-{
-    switch (kind) {
-    case K_F32: return group_fn_k<K_F32>(R, small);
-    case K_F64: return group_fn_k<K_F64>(R, small);
-    case K_B1: return group_fn_k<K_B1>(R, small);
-    case K_B4: return group_fn_k<K_B4>(R, small);
-    case K_B8: return group_fn_k<K_B8>(R, small);
-    default: return nullptr;
-    }
-}
+static int shape_warps(int warps) { return warps ? warps : kBatchWarps; }
 
-int group_occupancy(int kind, int R, int *sms, int *per_sm)
+int group_occupancy(int kind, int R, int *sms, int *per_sm, int warps)
 {
-    const void *fn = group_kernel(kind, R);
+    const int w = shape_warps(warps);
+    const void *fn = group_kernel(kind, R, w, false, false);
     if (!fn) return FT_EINVAL;
-    const int warps = kBatchWarps;
-    return occupancy(fn, warps * 32, kSmemBytes, sms, per_sm);
+    return occupancy(fn, w * 32, kSmemBytes, sms, per_sm);
 }
 
-// One CTA per kBatchWarps tiles, at most the resident CTAs of the whole GPU
-// and at most max_ctas (0 = no limit).
-static int group_grid(const void *fn, unsigned long long total_tiles, int ctas_per_sm, int max_ctas, unsigned *grid)
+// One CTA per `warps` tiles, at most the resident CTAs of the whole GPU and at
+// most max_ctas (0 = no limit).
+static int group_grid(const void *fn, int warps, unsigned long long total_tiles, int ctas_per_sm, int max_ctas,
+                      unsigned *grid)
 {
     int sms = 0, per_sm = 0;
-    const int rc = occupancy(fn, kBatchWarps * 32, kSmemBytes, &sms, &per_sm);
+    const int rc = occupancy(fn, warps * 32, kSmemBytes, &sms, &per_sm);
     if (rc != FT_OK) return rc;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     unsigned long long g = (unsigned long long)sms * per_sm;
     if (max_ctas > 0 && g > (unsigned long long)max_ctas) g = (unsigned long long)max_ctas;
-    const unsigned long long need = (total_tiles + kBatchWarps - 1) / kBatchWarps;
+    const unsigned long long need = (total_tiles + warps - 1) / warps;
     *grid = (unsigned)(g < need ? g : need);
     return FT_OK;
 }
 
 int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s, int max_ctas)
 {
-    const void *fn = group_kernel(g.kind, g.R);
+    const int w = shape_warps(g.warps);
+    const void *fn = group_kernel(g.kind, g.R, w, g.pf != 0, false);
     if (!fn) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
     unsigned grid = 0;
-    const int rc = group_grid(fn, g.total_tiles, ctas_per_sm, max_ctas, &grid);
+    const int rc = group_grid(fn, w, g.total_tiles, ctas_per_sm, max_ctas, &grid);
     if (rc != FT_OK) return rc;
     GroupDev arg = g;
     void *params[] = {&arg};
-    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBatchWarps * 32), params, kSmemBytes, s);
+    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(w * 32), params, kSmemBytes, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return check_launch(1);
 }
 
 int launch_small_group(const SmallGroup &g, cudaStream_t s, int max_ctas)
 {
-    const void *fn = group_kernel(g.kind, g.R, true);
+    const int w = shape_warps(g.warps);
+    const void *fn = group_kernel(g.kind, g.R, w, false, true);
     if (!fn || g.ntasks < 1 || g.ntasks > kSmallTasks) return FT_EINVAL;
     if (g.total_tiles == 0) return FT_OK;
     unsigned grid = 0;
-    const int rc = group_grid(fn, g.total_tiles, 0, max_ctas, &grid);
+    const int rc = group_grid(fn, w, g.total_tiles, 0, max_ctas, &grid);
     if (rc != FT_OK) return rc;
     void *params[] = {const_cast<SmallGroup *>(&g)};
-    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBatchWarps * 32), params, kSmemBytes, s);
+    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(w * 32), params, kSmemBytes, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return check_launch(1);
 }
@@ -385,7 +229,8 @@ struct ft_plan {
     std::vector<ftv::GroupDev> gd;
     uint8_t *dev = nullptr;
     size_t dev_bytes = 0;
-    ft_tune tune{0, 0};
+    ft_tune tune{0, 0, 0, 0};
+    std::map<std::pair<int, int>, std::pair<int, int>> shape;   // (kind, R) -> (warps, prefetch)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
@@ -393,6 +238,17 @@ struct ft_plan {
 };
 
 namespace ftv {
+
+// Launch shape of each group from the plan's choices (16 warps without the
+// prefetch where none was made).
+static void apply_shapes(ft_plan *p)
+{
+    for (GroupDev &g : p->gd) {
+        auto it = p->shape.find({g.kind, g.R});
+        g.warps = it == p->shape.end() ? kBatchWarps : it->second.first;
+        g.pf = it == p->shape.end() ? 0 : it->second.second;
+    }
+}
 
 static int upload_layout(ft_plan *p, int tile_blocks)
 {
@@ -411,102 +267,9 @@ static int upload_layout(ft_plan *p, int tile_blocks)
     }
     std::vector<uint8_t> host(need);
     p->layout.pack(host.data(), p->dev, p->gd);
+    apply_shapes(p);
     cudaError_t e = cudaMemcpy(p->dev, host.data(), need, cudaMemcpyHostToDevice);
     return e == cudaSuccess ? FT_OK : cuda_fail(e);
-}
-
-// In-process autotune cache keyed by a coarse signature of the batch.
-static std::mutex g_tune_mu;
-static std::map<std::string, ft_tune> g_tune_cache;
-
-static std::string signature(const std::vector<TaskArgs> &args)
-{
-    unsigned long long bytes = 0, blocks = 0;
-    std::map<std::pair<int, int>, int> mix;
-    for (const TaskArgs &a : args) {
-        blocks += a.nfull + (a.tail_bytes ? 1 : 0);
-        bytes += (a.nfull * 4096ull + a.tail_bytes) * (a.R + 1);
-        mix[{a.kind, a.R}]++;
-    }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    char buf[256];
-    int lb = 0;
-    while ((bytes >> lb) > 1) ++lb;
-    std::snprintf(buf, sizeof buf, "dev%d:n%zu:b2^%d:blk%llu", dev, args.size(), lb, blocks / std::max<size_t>(1, args.size()));
-    std::string s(buf);
-    for (auto &kv : mix) s += ":" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second);
-    return s;
-}
-
-static int time_config(ft_plan *p, const ft_tune &t, cudaStream_t s, float *best_ms)
-{
-    int rc = upload_layout(p, t.tile_blocks);
-    if (rc != FT_OK) return rc;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    rc = launch_batch(p->layout, p->gd, t.ctas_per_sm, s);   // warm-up
-    for (int rep = 0; rep < 3 && rc == FT_OK; ++rep) {
-        cudaEventRecord(e0, s);
-        rc = launch_batch(p->layout, p->gd, t.ctas_per_sm, s);
-        cudaEventRecord(e1, s);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) rc = cuda_fail(e);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        best = std::min(best, ms);
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    *best_ms = best;
-    return rc;
-}
-
-static int autotune(ft_plan *p, ft_tune *out)
-{
-    const std::string key = signature(p->args);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
-            *out = it->second;
-            return FT_OK;
-        }
-    }
-    cudaStream_t s;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(e);
-    int max_occ = 1;
-    for (const TaskArgs &a : p->args) {
-        int sms = 0, occ = 0;
-        if (group_occupancy(a.kind, a.R, &sms, &occ) == FT_OK) max_occ = std::max(max_occ, occ);
-    }
-    const int tiles[] = {1, 2, 4, 8, 16, 32};
-    ft_tune best{8, 0};
-    float best_ms = 1e30f;
-    int rc = FT_OK;
-    for (int tb : tiles) {
-        for (int cps = 1; cps <= max_occ && rc == FT_OK; ++cps) {
-            ft_tune t{tb, cps};
-            float ms = 0;
-            rc = time_config(p, t, s, &ms);
-            if (rc == FT_OK && ms < best_ms) {
-                best_ms = ms;
-                best = t;
-            }
-        }
-    }
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-    if (rc != FT_OK) return rc;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = best;
-    }
-    *out = best;
-    return FT_OK;
 }
 
 // Records the reset and the group kernels into the capture of stream s, the
@@ -545,8 +308,13 @@ static int launch_batch_branches(ft_plan *p, cudaStream_t s)
     return rc;
 }
 
-static int capture(ft_plan *p)
+// Captures the plan's current layout and shapes into an executable graph:
+// the reset, then the groups as parallel branches.  *kernels receives the
+// kernel launches one replay makes.
+static int build_exec(ft_plan *p, cudaGraph_t *graph, cudaGraphExec_t *exec, unsigned long long *kernels)
 {
+    *graph = nullptr;
+    *exec = nullptr;
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -559,17 +327,158 @@ static int capture(ft_plan *p)
         e = cudaStreamEndCapture(s, &g);
         if (rc == FT_OK && e != cudaSuccess) rc = cuda_fail(e);
         if (rc == FT_OK) {
-            p->graph = g;
-            if ((e = cudaGraphInstantiate(&p->exec, g, 0)) != cudaSuccess) rc = cuda_fail(e);
+            *graph = g;
+            if ((e = cudaGraphInstantiate(exec, g, 0)) != cudaSuccess) rc = cuda_fail(e);
         } else if (g) {
             cudaGraphDestroy(g);
         }
     }
     cudaStreamDestroy(s);
     // the launches recorded during capture did not run; a replay makes them
-    p->graph_kernels = g_launches.load() - before;
-    g_launches.fetch_sub(p->graph_kernels, std::memory_order_relaxed);
+    *kernels = g_launches.load() - before;
+    g_launches.fetch_sub(*kernels, std::memory_order_relaxed);
     return rc;
+}
+
+// In-process autotune cache keyed by a coarse signature of the batch.
+struct TuneResult {
+    int tile_blocks;
+    std::map<std::pair<int, int>, std::pair<int, int>> shape;
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneResult> g_tune_cache;
+
+static std::string signature(const std::vector<TaskArgs> &args)
+{
+    unsigned long long bytes = 0, blocks = 0;
+    std::map<std::pair<int, int>, int> mix;
+    for (const TaskArgs &a : args) {
+        blocks += a.nfull + (a.tail_bytes ? 1 : 0);
+        bytes += (a.nfull * 4096ull + a.tail_bytes) * (a.R + 1);
+        mix[{a.kind, a.R}]++;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    char buf[256];
+    int lb = 0;
+    while ((bytes >> lb) > 1) ++lb;
+    std::snprintf(buf, sizeof buf, "dev%d:n%zu:b2^%d:blk%llu", dev, args.size(), lb, blocks / std::max<size_t>(1, args.size()));
+    std::string s(buf);
+    for (auto &kv : mix) s += ":" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second);
+    return s;
+}
+
+// Time of one replay of the plan as it stands (layout uploaded, shapes set):
+// the graph that ft_vote_batched would replay is built and replayed, one
+// warm-up and the best of three.
+static int time_replay(ft_plan *p, cudaStream_t s, float *best_ms)
+{
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    unsigned long long kernels = 0;
+    int rc = build_exec(p, &g, &x, &kernels);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    if (rc == FT_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaError_t e = cudaGraphLaunch(x, s);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+            if ((e = cudaGraphLaunch(x, s)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+    *best_ms = best;
+    return rc;
+}
+
+// The autotuner.  It times the graph that will be replayed, with the groups
+// as the parallel branches they will be: first the tile size (4 KiB blocks per
+// work tile) with every group at 16 warps, then, at that tile size, each
+// group's launch shape in turn (warps per CTA 8, 12 or 16, with and without
+// the L2 prefetch of the tile's next block), the other groups keeping theirs.
+// A voter CTA fills an SM's shared memory with the CRC tables, so one CTA per
+// SM is the only residency there is to choose.  Shapes forced by the caller
+// (ft_tune.warps / l2_prefetch) are not searched.
+static int autotune(ft_plan *p, const ft_tune *forced, TuneResult *out)
+{
+    const std::string key = signature(p->args);
+    const bool free_shape = !forced || (forced->warps == 0 && forced->l2_prefetch == 0);
+    const bool free_tile = !forced || forced->tile_blocks == 0;
+    if (free_shape && free_tile) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            return FT_OK;
+        }
+    }
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = FT_OK;
+    TuneResult best;
+    best.tile_blocks = free_tile ? 8 : forced->tile_blocks;
+    best.shape = p->shape;
+    float best_ms = 1e30f;
+    if (free_tile) {
+        for (int tb : {1, 2, 4, 8, 16, 32}) {
+            float ms = 0;
+            if ((rc = upload_layout(p, tb)) != FT_OK || (rc = time_replay(p, s, &ms)) != FT_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.tile_blocks = tb;
+            }
+        }
+    }
+    if (rc == FT_OK && free_shape) {
+        rc = upload_layout(p, best.tile_blocks);
+        if (rc == FT_OK && !free_tile) rc = time_replay(p, s, &best_ms);
+        std::vector<std::pair<int, int>> groups;
+        for (const GroupHost &gh : p->layout.groups)
+            if (gh.tiles) groups.push_back({gh.kind, gh.R});
+        for (size_t gi = 0; gi < groups.size() && rc == FT_OK; ++gi) {
+            for (int w : kShapeWarps) {
+                for (int pf = 0; pf <= 1 && rc == FT_OK; ++pf) {
+                    if (w == kBatchWarps && pf == 0) continue;        // the shape timed already
+                    p->shape = best.shape;
+                    p->shape[groups[gi]] = {w, pf};
+                    apply_shapes(p);
+                    float ms = 0;
+                    if ((rc = time_replay(p, s, &ms)) != FT_OK) break;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best.shape = p->shape;
+                    }
+                }
+            }
+        }
+        p->shape = best.shape;
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc != FT_OK) return rc;
+    if (free_shape && free_tile) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    *out = best;
+    return FT_OK;
+}
+
+static int capture(ft_plan *p)
+{
+    return build_exec(p, &p->graph, &p->exec, &p->graph_kernels);
 }
 
 }  // namespace ftv
@@ -582,7 +491,9 @@ int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks, co
     if (!plan || ntasks < 0 || (ntasks > 0 && !tasks)) return FT_EINVAL;
     *plan = nullptr;
     if (tune && ((tune->tile_blocks && (tune->tile_blocks < 1 || tune->tile_blocks > 64)) ||
-                 tune->ctas_per_sm < 0 || tune->ctas_per_sm > 8))
+                 tune->ctas_per_sm < 0 || tune->ctas_per_sm > 8 ||
+                 (tune->warps != 0 && tune->warps != 8 && tune->warps != 12 && tune->warps != 16) ||
+                 tune->l2_prefetch < 0 || tune->l2_prefetch > 2))
         return FT_EINVAL;
     ft_plan *p = new (std::nothrow) ft_plan();
     if (!p) return FT_ENOMEM;
@@ -595,23 +506,61 @@ int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks, co
         }
         p->args.push_back(make_task_args(&tasks[i]));
     }
+    if (tune) p->tune = *tune;
+    p->tune.ctas_per_sm = tune ? tune->ctas_per_sm : 0;
+    const bool forced_shape = tune && (tune->warps != 0 || tune->l2_prefetch != 0);
+    if (forced_shape) {
+        // the caller's shape for every group
+        for (const TaskArgs &a : p->args)
+            p->shape[{a.kind, a.R}] = {tune->warps ? tune->warps : kBatchWarps, tune->l2_prefetch == 2 ? 1 : 0};
+    }
     int rc = FT_OK;
-    if (!tune || tune->tile_blocks == 0 || tune->ctas_per_sm == 0) {
-        ft_tune t{};
-        rc = autotune(p, &t);
-        if (rc == FT_OK && tune && tune->tile_blocks) t.tile_blocks = tune->tile_blocks;
-        if (rc == FT_OK && tune && tune->ctas_per_sm) t.ctas_per_sm = tune->ctas_per_sm;
-        p->tune = t;
-    } else {
-        p->tune = *tune;
+    if (!tune || tune->tile_blocks == 0 || !forced_shape) {
+        TuneResult t;
+        rc = autotune(p, tune, &t);
+        if (rc == FT_OK) {
+            p->tune.tile_blocks = t.tile_blocks;
+            if (!forced_shape) p->shape = t.shape;
+        }
     }
     if (rc == FT_OK) rc = upload_layout(p, p->tune.tile_blocks);
+    if (rc == FT_OK) {
+        // report a shape common to every group, else 0
+        int w = -1, pf = -1;
+        for (const GroupDev &g : p->gd) {
+            if (!g.total_tiles) continue;
+            w = (w == -1 || w == g.warps) ? g.warps : 0;
+            pf = (pf == -1 || pf == g.pf + 1) ? g.pf + 1 : 0;
+        }
+        p->tune.warps = w < 0 ? kBatchWarps : w;
+        p->tune.l2_prefetch = pf < 0 ? 1 : pf;
+    }
     if (rc == FT_OK) rc = capture(p);
     if (rc != FT_OK) {
         ft_plan_destroy(p);
         return rc;
     }
     *plan = p;
+    return FT_OK;
+}
+
+int ft_plan_groups(const ft_plan *p, ft_plan_group *out, int32_t max, int32_t *n)
+{
+    if (!p || !n || max < 0 || (max > 0 && !out)) return FT_EINVAL;
+    static const int32_t kDtypeOfKind[] = {FT_F32, FT_F64, FT_U8, FT_I32, FT_I64};
+    int k = 0;
+    for (size_t i = 0; i < p->gd.size() && k < max; ++i, ++k) {
+        const ftv::GroupDev &g = p->gd[i];
+        const ftv::GroupHost &gh = p->layout.groups[i];
+        out[k].dtype = kDtypeOfKind[g.kind];
+        out[k].R = g.R;
+        out[k].tasks = gh.t1 - gh.t0;
+        out[k].warps = g.warps ? g.warps : ftv::kBatchWarps;
+        out[k].l2_prefetch = g.pf;
+        out[k].tile_blocks = g.tile_blocks;
+        out[k].tiles = g.total_tiles;
+    }
+    *n = (int32_t)p->gd.size();
     return FT_OK;
 }
 

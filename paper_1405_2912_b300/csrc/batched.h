@@ -11,11 +11,30 @@
 
 namespace ftv {
 
-// Warps per CTA of the batched kernels: 16 for every (kind, R), without the
-// L2 prefetch that a single large f32 R = 3 vote gains from.  On the batch of
-// 4096 tasks of 4 KiB .. 16 MiB this measured 0.621 M tasks/s (6.48 TB/s)
-// against 0.599 M (6.25 TB/s) with the single-task shapes.
+// Launch shapes of the batched kernels: warps per CTA (8, 12 or 16) and
+// whether a warp prefetches its tile's next block into L2.  A plan's
+// autotuner picks one per (kind, R) group; without tuning a group runs 16
+// warps without prefetch, which on the batch of 4096 tasks of 4 KiB .. 16 MiB
+// measured 0.621 M tasks/s (6.48 TB/s) against 0.599 M (6.25 TB/s) with the
+// single-task shapes.  The small-batch kernel is built with 8 and 16 warps.
 constexpr int kBatchWarps = 16;
+constexpr int kShapeWarps[] = {8, 12, 16};
+
+// The kernel of a (kind, R) group in one launch shape: the plan's persistent
+// kernel (small = false) or the small-batch kernel whose group travels in its
+// parameters (small = true; built without the prefetch).  Each warp count's
+// kernels are instantiated in a translation unit of their own
+// (batched_w8.cu, batched_w12.cu, batched_w16.cu) so that they compile in
+// parallel; nullptr for a shape that is not built.
+template <int W>
+const void *group_fn_w(int kind, int R, bool pf, bool small);
+template <>
+const void *group_fn_w<8>(int kind, int R, bool pf, bool small);
+template <>
+const void *group_fn_w<12>(int kind, int R, bool pf, bool small);
+template <>
+const void *group_fn_w<16>(int kind, int R, bool pf, bool small);
+const void *group_kernel(int kind, int R, int warps, bool pf, bool small);
 
 // A (kind, R) group of a small batch, passed whole as the kernel parameter:
 // no upload precedes the launch.  tile_first[t] is task t's first tile (an
@@ -35,6 +54,8 @@ struct SmallGroup {
     int32_t tile_blocks;
     int32_t kind;
     int32_t R;
+    int32_t warps;                   // 8 or 16 (0 = 16)
+    int32_t pad_;
 };
 int launch_small_group(const SmallGroup &g, cudaStream_t s, int max_ctas = 0);
 

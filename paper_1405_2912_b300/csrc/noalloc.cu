@@ -247,6 +247,8 @@ static int vote_batched_noalloc(const ft_vote_desc *descs, int ntasks, int tile_
     }
     const size_t smem = kSmemBytes;
     if (auto_tile) {
+        // every group kernel holds a whole SM's shared memory (one CTA per
+        // SM) with the same warps, so the first group's wave stands for all
         unsigned long long total = 0;
         for (int i = 0; i < ntasks; ++i) total += tasks_h[i].nfull + (tasks_h[i].tail_bytes ? 1 : 0);
         const TaskArgs &a0 = tasks_h[0];

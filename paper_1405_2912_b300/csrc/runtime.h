@@ -52,6 +52,8 @@ struct GroupDev {
     int32_t kind;
     int32_t R;
     int32_t t0, t1;
+    int32_t warps;                   // launch shape: warps per CTA (8, 12, 16; 0 = 16)
+    int32_t pf;                      // and the L2 prefetch of the tile's next block
     int32_t pad_;
 };
 
@@ -60,8 +62,9 @@ int launch_batch_reset(const TaskArgs *tasks, int ntasks, unsigned long long *co
                        cudaStream_t s);
 // Launch the persistent batched voter for one group.
 int launch_group(const GroupDev &g, int ctas_per_sm, cudaStream_t s, int max_ctas = 0);
-// Resident CTAs per SM of the batched kernel for (kind, R) and the SM count.
-int group_occupancy(int kind, int R, int *sms, int *per_sm);
+// Resident CTAs per SM of the batched kernel for (kind, R) with `warps` warps
+// per CTA (0 = 16), and the SM count.
+int group_occupancy(int kind, int R, int *sms, int *per_sm, int warps = 0);
 // Tile size of a batch whose caller left it to the library: 8 blocks, halved
 // while the batch's total_blocks would make fewer tiles than the kernel has
 // warps in one wave (wave_warps), so that a small batch is spread over as

@@ -56,7 +56,14 @@ class ft_vote_desc(ctypes.Structure):
 
 
 class ft_tune(ctypes.Structure):
-    _fields_ = [("tile_blocks", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("tile_blocks", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("warps", ctypes.c_int32),
+                ("l2_prefetch", ctypes.c_int32)]
+
+
+class ft_plan_group(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("R", ctypes.c_int32), ("tasks", ctypes.c_int32),
+                ("warps", ctypes.c_int32), ("l2_prefetch", ctypes.c_int32), ("tile_blocks", ctypes.c_int32),
+                ("tiles", ctypes.c_uint64)]
 
 
 class ft_server_config(ctypes.Structure):
@@ -89,6 +96,7 @@ class ft_server_stats(ctypes.Structure):
 
 
 assert ctypes.sizeof(ft_stats) == 144
+assert ctypes.sizeof(ft_plan_group) == 32
 assert ctypes.sizeof(ft_vote_desc) == 8 * FT_MAX_R + 8 + 8 + 16 + 24
 
 _P = ctypes.c_void_p
@@ -111,6 +119,8 @@ ft_vote_batched = _sig("ft_vote_batched", ctypes.c_int, _P, _P)
 ft_vote_batched_nograph = _sig("ft_vote_batched_nograph", ctypes.c_int, _P, _P)
 ft_plan_tune = _sig("ft_plan_tune", ctypes.c_int, _P, ctypes.POINTER(ft_tune))
 ft_plan_destroy = _sig("ft_plan_destroy", ctypes.c_int, _P)
+ft_plan_groups = _sig("ft_plan_groups", ctypes.c_int, _P, ctypes.POINTER(ft_plan_group), ctypes.c_int32,
+                      ctypes.POINTER(ctypes.c_int32))
 ft_server_create = _sig("ft_server_create", ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(ft_server_config))
 ft_submit = _sig("ft_submit", ctypes.c_int, _P, ctypes.POINTER(ft_vote_desc), ctypes.POINTER(ctypes.c_uint64))
 ft_poll = _sig("ft_poll", ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ft_result))
