@@ -288,7 +288,8 @@ __device__ __noinline__ void slot_finish(const SlotRef &sr, ft_stats *user)
 // sub-batch.
 //
 // The kernel is always launched as a programmatic dependent of the kernel
-// before it in the stream, and lets the kernel after it launch at once.
+// before it in the stream, and lets the kernel after it launch once its own
+// CTAs have voted their blocks.
 // Before it waits for its predecessor it asks L2 for the warp's first block
 // of every replica (L2 is the device's point of coherence, so early lines are
 // never stale) and copies the CRC tables into shared memory; it reads the
@@ -300,7 +301,6 @@ template <int K, int R, int W, bool PF, int JB>
 __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a, const SlotRef sr)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    pdl_release();
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned long long step = (unsigned long long)gridDim.x * W;
@@ -322,6 +322,10 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a, const
         vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
         st.merge(ts);
     }
+    // Only now may the next kernel's CTAs launch: one released at the start
+    // would take SMs (a voter CTA holds an SM's shared memory) and sit in its
+    // wait while this kernel votes, keeping other streams' work off them.
+    pdl_release();
     if (sr.slot) {
         st.flush(&sr.slot->s, lane);
         slot_finish(sr, a.stats);
