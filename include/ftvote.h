@@ -271,6 +271,13 @@ typedef struct ft_server_config {
                                    (R+1)*n*sizeof(dtype) bytes stay within this, and at least
                                    one (0 = no limit): bounds how long a small request waits
                                    for the large ones packed with it */
+    int32_t  reserved_sms;      /* with two or more streams, SMs that no batch's kernels fill,
+                                   so that a batch arriving behind a large one finds SMs free:
+                                   0 = 32, -1 = none, else 1 .. SM count - 1 */
+    int32_t  idle_spin_us;      /* how long the worker thread keeps polling (one CPU core busy)
+                                   after its last batch before it sleeps until the next request;
+                                   a request that finds it asleep waits for a thread wake-up
+                                   (tens of microseconds): 0 = 2000, -1 = do not poll */
 } ft_server_config;
 
 typedef struct ft_result {
@@ -279,15 +286,20 @@ typedef struct ft_result {
     uint64_t n;
     ft_stats stats;             /* copy of the request's statistics              */
     double   submit_us;         /* host clock (monotonic, microseconds) at submit */
-    double   done_us;           /* host clock when the worker saw the batch complete */
+    double   done_us;           /* host clock when the server saw the batch complete */
+    double   launch_us;         /* host clock when the request's batch began to launch */
+    double   launched_us;       /* host clock when its launch calls had returned */
 } ft_result;
 
 /* Start a server: one host thread that packs admitted requests into batches
  * and launches them on `streams` CUDA streams of the current device (each
  * with up to three auxiliary streams, on which a batch's further element-type
  * / R groups run in parallel).  With two or more streams no batch's kernels
- * occupy more than all but 16 SMs, so that a batch is not held behind all of
- * a large one.  Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
+ * occupy more than all but cfg->reserved_sms SMs, so that a batch is not held
+ * behind all of a large one.  The thread polls for new requests and finished
+ * batches without holding the server's lock, and keeps polling for
+ * cfg->idle_spin_us after its last batch before it sleeps.
+ * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
 int ft_server_create(ft_server **srv, const ft_server_config *cfg);
 
 /* Admit one request (the replicas must already hold the duplicated results).
@@ -350,6 +362,7 @@ typedef struct ft_server_stats {
     uint64_t inflight_bytes;         /* their share of the budget                        */
     double   launch_host_us;         /* worker time spent laying out and launching batches */
     double   batch_span_us;          /* summed launch -> completion time of the batches    */
+    double   queue_us;               /* summed submit -> taken into a batch time of the requests */
 } ft_server_stats;
 int ft_server_info(ft_server *srv, ft_server_stats *out);
 

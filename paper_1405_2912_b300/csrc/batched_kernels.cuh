@@ -84,7 +84,10 @@ struct ScanLookup {
 // and the first index it sees per replica is its minimum.  PF: lanes 0..R-1
 // prefetch the tile's next block into L2 while the warp votes the current one.
 // ---------------------------------------------------------------------------
-template <int K, int R, bool PF, class Lookup>
+// STATIC: warp w of the grid takes tiles w, w + (warps in the grid), ...
+// instead of claiming them, which saves a round trip to the counter per tile
+// where the tiles are too few for their sizes to need balancing.
+template <int K, int R, bool PF, bool STATIC, class Lookup>
 __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long *counter, unsigned long long total_tiles,
                                            int tile_blocks, const uint32_t *s_crc)
 {
@@ -95,10 +98,17 @@ __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long 
     st.init();
     int cur = -1;
     ft_stats *cur_stats = nullptr;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long next = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (;;) {
         unsigned long long tg = 0;
-        if (lane == 0) tg = atomicAdd(counter, 1ull);
-        tg = __shfl_sync(0xFFFFFFFFu, tg, 0);
+        if constexpr (STATIC) {
+            tg = next;
+            next += nwarps;
+        } else {
+            if (lane == 0) tg = atomicAdd(counter, 1ull);
+            tg = __shfl_sync(0xFFFFFFFFu, tg, 0);
+        }
         if (tg >= total_tiles) break;
         const int t = lk.task_of(tg, lane);
         const TaskArgs a = lk.tasks[t];
@@ -130,24 +140,37 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
     load_crc_tables<W>(s_crc);
     __syncthreads();
-    vote_tiles<K, R, PF>(MapLookup{g.tasks, g.tile_task, g.tile_first}, g.counter, g.total_tiles, g.tile_blocks,
-                         s_crc);
+    vote_tiles<K, R, PF, false>(MapLookup{g.tasks, g.tile_task, g.tile_first}, g.counter, g.total_tiles,
+                                g.tile_blocks, s_crc);
     if (g.done_ctas)
         copy_out_if_last(CopyOut{g.done_ctas, nullptr, g.tasks + g.t0, g.t1 - g.t0, false, g.stats_base, g.stats_out});
 }
 
 // The same voter for a small batch whose whole group travels in the kernel
 // parameters (no upload); its counters and statistics are left reset for the
-// next launch by the last CTA.
+// next launch by the last CTA.  Its warps take their tiles in a fixed order
+// (the batch is small enough not to need balancing).
 template <int K, int R, int W>
 __global__ void __launch_bounds__(W * 32, 1) batched_small_kernel(const __grid_constant__ SmallGroup g)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
+    const ScanLookup lk{g.tasks, g.tile_first, g.ntasks};
+    {
+        // ask L2 for the first block of the warp's first tile while the CRC
+        // tables are copied
+        const int lane = threadIdx.x & 31;
+        const unsigned long long tg = (unsigned long long)blockIdx.x * W + (threadIdx.x >> 5);
+        if (tg < g.total_tiles) {
+            const int t = lk.task_of(tg, lane);
+            const TaskArgs &a = g.tasks[t];
+            const unsigned long long b0 = (tg - g.tile_first[t]) * (unsigned long long)g.tile_blocks;
+            if (lane < R && b0 < a.nfull) prefetch_l2(a.rep[lane] + b0 * kBlockBytes, kBlockBytes);
+        }
+    }
     load_crc_tables<W>(s_crc);
     __syncthreads();
-    vote_tiles<K, R, false>(ScanLookup{g.tasks, g.tile_first, g.ntasks}, g.counter, g.total_tiles, g.tile_blocks,
-                            s_crc);
+    vote_tiles<K, R, false, true>(lk, g.counter, g.total_tiles, g.tile_blocks, s_crc);
     copy_out_if_last(CopyOut{g.done_ctas, g.counter, g.tasks, g.ntasks, true, g.stats_base, g.stats_out});
 }
 

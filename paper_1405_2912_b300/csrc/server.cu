@@ -13,6 +13,7 @@
 // bound, as the paper's runtime bounds the wait for a task by a timeout
 // (Sec. IV.C).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -40,7 +41,7 @@ struct Request {
     ftv::TaskArgs args;
     ft_stats *user_stats = nullptr;
     unsigned long long bytes = 0;
-    double submit_us = 0, done_us = 0;
+    double submit_us = 0, done_us = 0, launch_us = 0, launched_us = 0;
     int status = FT_EAGAIN;
     bool done = false;
     ft_stats result;
@@ -54,6 +55,7 @@ struct Slot {
     uint8_t *host = nullptr;           // batch layout staging (pinned)
     size_t host_cap = 0;
     double launched_at = 0.0;          // worker clock when the batch began to launch
+    double launch_done_at = 0.0;       // and when its launch calls had returned
     ft_stats *host_stats = nullptr;    // pinned copy of the batch's statistics, read once the event completes
     ft_stats *host_stats_dev = nullptr;   // the same memory as the device addresses it
     ft_stats **dev_user = nullptr;     // caller stats pointers (scatter targets)
@@ -151,7 +153,10 @@ struct ft_server {
     // counters reported by ft_server_info
     unsigned long long batches = 0, batched_requests = 0, completed = 0;
     int busy_now = 0, busy_max = 0;
-    double launch_host_us = 0.0, batch_span_us = 0.0;
+    double launch_host_us = 0.0, batch_span_us = 0.0, queue_us = 0.0;
+    // bumped (under the lock) whenever there is something new for the worker:
+    // an admitted request, a pause change or stop
+    std::atomic<unsigned long long> version{0};
 };
 
 namespace {
@@ -168,6 +173,8 @@ void complete_slot(ft_server *s, int si, double t)
         r.status = sl.status;
         r.done = true;
         r.done_us = t;
+        r.launch_us = sl.launched_at;
+        r.launched_us = sl.launch_done_at;
     }
     if (sl.last_small && sl.status != FT_OK) sl.small_dirty = true;
     s->completed += sl.tickets.size();
@@ -212,17 +219,20 @@ int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
 // SMs that no batch's kernels may fill while the server has several streams:
 // a voter CTA holds a whole SM (its CRC tables), so without them a batch that
 // arrives behind a large one waits for all of the large one's CTAs to exit.
-// Six replays each at 20k and 60k requests/s, continuous batching, medians:
-// p99 0.36 -> 0.29 ms and 1.11 -> 0.92 ms with 16 (32: 0.31 and 0.94 ms);
-// p50 and the one-request batches unchanged within the replays' spread.
-constexpr int kReservedSms = 16;
+// Replays of the 20k and 60k requests/s streams, continuous batching, 3
+// streams: none reserved p99 0.36 / 1.11 ms, 16 SMs 0.29 / 0.92 ms, and 32 SMs
+// 0.22 / 0.64 ms (16: 0.24 / 0.87 ms in the same run) once the worker polled
+// without holding the server's lock; p50 within the runs' spread.
+// ft_server_config.reserved_sms overrides it.
+constexpr int kReservedSms = 32;
 
 int batch_max_ctas(const ft_server *s, const ftv::TaskArgs &a)
 {
-    if (s->slots.size() < 2 || kReservedSms == 0) return 0;
+    const int reserve = s->cfg.reserved_sms == 0 ? kReservedSms : s->cfg.reserved_sms;
+    if (s->slots.size() < 2 || reserve <= 0) return 0;
     int sms = 0, per_sm = 0;
     if (ftv::group_occupancy(a.kind, a.R, &sms, &per_sm) != FT_OK) return 0;
-    return (sms - kReservedSms) * per_sm;
+    return sms > reserve ? (sms - reserve) * per_sm : per_sm;
 }
 
 // Warps per CTA of a group of `tiles` work tiles that may use `max_ctas` CTAs
@@ -378,8 +388,19 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
 }
 
 // Idle time the worker spins (yielding) before it sleeps on the condition
-// variable: a request that arrives within it is picked up without a wake-up.
-constexpr double kSpinUs = 200.0;
+// variable, unless the configuration says otherwise: a request that arrives
+// within it is picked up without a wake-up.  A wake-up measured 50 to 70 us
+// on the GPU host; at 20k requests/s (Poisson) 2 % of the gaps between
+// requests exceed 200 us, about none 2 ms.
+constexpr double kSpinUs = 2000.0;
+
+// Longest stretch the worker polls without taking the lock.
+constexpr double kPollSliceUs = 50.0;
+
+double idle_spin_us(const ft_server *s)
+{
+    return s->cfg.idle_spin_us == 0 ? kSpinUs : s->cfg.idle_spin_us < 0 ? 0.0 : (double)s->cfg.idle_spin_us;
+}
 
 void worker_main(ft_server *s)
 {
@@ -407,9 +428,23 @@ void worker_main(ft_server *s)
         // 2. nothing to launch: spin while batches are in flight or shortly
         //    after the last activity, else sleep until a request or stop
         if (s->stop || s->paused || s->pending.empty() || free_slot < 0) {
-            if (any_busy || now_us() - idle_since < kSpinUs) {
+            if (any_busy || now_us() - idle_since < idle_spin_us(s)) {
+                // wait for a change without holding the lock, so that clients
+                // calling ft_submit / ft_poll meanwhile never queue behind
+                // the worker: a new request, pause or stop (the state
+                // version), or a batch in flight completing
+                int nb = 0;
+                cudaEvent_t ev[8];
+                for (size_t i = 0; i < s->slots.size(); ++i)
+                    if (s->slots[i].busy) ev[nb++] = s->slots[i].done;
+                const unsigned long long ver = s->version.load(std::memory_order_acquire);
+                const double t_end = now_us() + kPollSliceUs;
                 lk.unlock();
-                std::this_thread::yield();
+                for (bool changed = false; !changed && now_us() < t_end;) {
+                    changed = s->version.load(std::memory_order_acquire) != ver;
+                    for (int k = 0; k < nb && !changed; ++k) changed = cudaEventQuery(ev[k]) != cudaErrorNotReady;
+                    if (!changed && nb == 0) std::this_thread::yield();
+                }
                 lk.lock();
             } else {
                 s->cv_work.wait(lk);
@@ -433,6 +468,7 @@ void worker_main(ft_server *s)
             if (!args.empty() && s->cfg.max_batch_bytes && batch_bytes + it->second.bytes > s->cfg.max_batch_bytes)
                 break;
             s->pending.pop_front();
+            s->queue_us += now_us() - it->second.submit_us;
             batch_bytes += it->second.bytes;
             args.push_back(it->second.args);
             sl.tickets.push_back(tk);
@@ -456,7 +492,8 @@ void worker_main(ft_server *s)
         if (rc == FT_OK) rc = launch_slot(s, free_slot, args, any_user);
         sl.status = rc;
         cudaError_t e = cudaEventRecord(sl.done, sl.stream);
-        const double launched = now_us() - sl.launched_at;
+        sl.launch_done_at = now_us();
+        const double launched = sl.launch_done_at - sl.launched_at;
         if (e != cudaSuccess) {
             // no completion event: finish the batch here
             cudaStreamSynchronize(sl.stream);
@@ -505,7 +542,8 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     if (!out || !cfg) return FT_EINVAL;
     *out = nullptr;
     if (cfg->mem_budget_bytes == 0 || cfg->max_slots < 1 || cfg->max_slots > 65536 || cfg->streams < 1 ||
-        cfg->streams > 8 || cfg->tile_blocks < 0 || cfg->tile_blocks > 64 || cfg->max_inflight < 0)
+        cfg->streams > 8 || cfg->tile_blocks < 0 || cfg->tile_blocks > 64 || cfg->max_inflight < 0 ||
+        cfg->reserved_sms < -1 || cfg->idle_spin_us < -1)
         return FT_EINVAL;
     ft_server *s = new (std::nothrow) ft_server();
     if (!s) return FT_ENOMEM;
@@ -586,6 +624,7 @@ int admit_locked(ft_server *s, const Request &r, uint64_t *ticket)
     const unsigned long long t = s->next_ticket++;
     s->reqs.emplace(t, r);
     s->pending.push_back(t);
+    s->version.fetch_add(1, std::memory_order_release);
     s->inflight_bytes += r.bytes;
     s->inflight += 1;
     *ticket = t;
@@ -624,6 +663,8 @@ void retire_locked(ft_server *s, std::unordered_map<unsigned long long, Request>
         res->stats = r.result;
         res->submit_us = r.submit_us;
         res->done_us = r.done_us;
+        res->launch_us = r.launch_us;
+        res->launched_us = r.launched_us;
     }
     s->inflight_bytes -= r.bytes;
     s->inflight -= 1;
@@ -704,6 +745,7 @@ int ft_server_pause(ft_server *s, int32_t paused)
     if (!s) return FT_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     s->paused = paused != 0;
+    s->version.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_all();
     return FT_OK;
 }
@@ -715,6 +757,7 @@ int ft_server_destroy(ft_server *s)
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
         s->pending.clear();
+        s->version.fetch_add(1, std::memory_order_release);
         s->cv_work.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
@@ -734,6 +777,7 @@ int ft_server_info(ft_server *s, ft_server_stats *out)
     out->inflight_bytes = s->inflight_bytes;
     out->launch_host_us = s->launch_host_us;
     out->batch_span_us = s->batch_span_us;
+    out->queue_us = s->queue_us;
     return FT_OK;
 }
 

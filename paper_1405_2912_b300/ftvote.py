@@ -72,7 +72,9 @@ class ft_server_config(ctypes.Structure):
                 ("streams", ctypes.c_int32),
                 ("tile_blocks", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32),
-                ("max_batch_bytes", ctypes.c_uint64)]
+                ("max_batch_bytes", ctypes.c_uint64),
+                ("reserved_sms", ctypes.c_int32),
+                ("idle_spin_us", ctypes.c_int32)]
 
 
 class ft_result(ctypes.Structure):
@@ -81,7 +83,9 @@ class ft_result(ctypes.Structure):
                 ("n", ctypes.c_uint64),
                 ("stats", ft_stats),
                 ("submit_us", ctypes.c_double),
-                ("done_us", ctypes.c_double)]
+                ("done_us", ctypes.c_double),
+                ("launch_us", ctypes.c_double),
+                ("launched_us", ctypes.c_double)]
 
 
 class ft_unit_rating(ctypes.Structure):
@@ -92,7 +96,7 @@ class ft_server_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_uint64), ("requests", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("max_batches_in_flight", ctypes.c_int32), ("inflight_requests", ctypes.c_int32),
                 ("inflight_bytes", ctypes.c_uint64), ("launch_host_us", ctypes.c_double),
-                ("batch_span_us", ctypes.c_double)]
+                ("batch_span_us", ctypes.c_double), ("queue_us", ctypes.c_double)]
 
 
 assert ctypes.sizeof(ft_stats) == 144

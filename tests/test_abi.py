@@ -82,7 +82,8 @@ def test_digest_argument_checks(fv):
 def test_server_config_validation(fv):
     srv = ctypes.c_void_p()
     for bad in [(0, 16, 2, 8, 0), (1 << 30, 0, 2, 8, 0), (1 << 30, 16, 0, 8, 0), (1 << 30, 16, 9, 8, 0),
-                (1 << 30, 16, 2, 65, 0), (1 << 30, 16, 2, -1, 0), (1 << 30, 16, 2, 8, -1)]:
+                (1 << 30, 16, 2, 65, 0), (1 << 30, 16, 2, -1, 0), (1 << 30, 16, 2, 8, -1),
+                (1 << 30, 16, 2, 8, 0, 0, -2)]:
         cfg = fv.ft_server_config(*bad)
         assert fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)) == fv.FT_EINVAL
     assert fv.ft_server_create(None, None) == fv.FT_EINVAL
