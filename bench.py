@@ -475,6 +475,7 @@ def batched_summary(b):
            "per_task_launches_tasks_per_s": b["per_task_launches"]["tasks_per_s"],
            "speedup_vs_per_task": b["speedup_vs_per_task"],
            "noalloc_tasks_per_s": b["noalloc"]["tasks_per_s"] if b.get("noalloc") else None,
+           "one_kernel_tasks_per_s": b["one_kernel_for_the_batch"]["tasks_per_s"],
            "launches_per_batch": b["launches_per_batch"], "tune": b["tune"]}
     return out
 
@@ -581,6 +582,13 @@ def run_batched(args, dev, stream):
         noalloc = {"tasks_per_s": round(len(specs) / t_n, 1), "gb_per_s": round(nbytes / t_n / 1e9, 1),
                    "ms_per_batch": round(t_n * 1e3, 3)}
     fv.ft_plan_destroy(plan)
+    # the same batch as one persistent kernel for all groups (the tuner's
+    # other candidate), tile size as chosen above
+    one = fv.ft_tune(tune.tile_blocks, 0, 0, 0, 1)
+    plan1 = ctypes.c_void_p()
+    fv.check(fv.ft_plan_create(ctypes.byref(plan1), descs, len(specs), ctypes.byref(one)), "ft_plan_create")
+    t_1 = timed(lambda: fv.check(fv.ft_vote_batched(plan1, sh), "batched"), args.batched_reps)
+    fv.ft_plan_destroy(plan1)
     del keep, stats
     torch.cuda.empty_cache()
     return {"workload": f"{len(specs)} tasks, n log-uniform [2^10, 2^22], f32/f64/i32 40/30/30 %, R=3, "
@@ -590,11 +598,14 @@ def run_batched(args, dev, stream):
             "ms_per_batch": round(t_b * 1e3, 3), "bytes_per_batch": nbytes,
             "launches_per_batch": int(launches_b),
             "tune": {"tile_blocks": tune.tile_blocks,
+                     "kernels": "one for the batch" if tune.kernels == 1 else "one per (dtype, R) group",
                      "groups": [f"{g['dtype']} R={g['R']}: {g['warps']} warps"
                                 f"{' + L2 prefetch' if g['l2_prefetch'] else ''}" for g in groups]},
             "per_task_launches": {"tasks_per_s": round(len(specs) / t_p, 1), "gb_per_s": round(nbytes / t_p / 1e9, 1),
                                   "ms_per_batch": round(t_p * 1e3, 3)},
             "speedup_vs_per_task": round(t_p / t_b, 2),
+            "one_kernel_for_the_batch": {"tasks_per_s": round(len(specs) / t_1, 1),
+                                         "gb_per_s": round(nbytes / t_1 / 1e9, 1)},
             "noalloc": noalloc,
             "setup_s": {"generate_upload": round(gen_s, 1), "plan_create_autotune": round(plan_s, 2)}}
 

@@ -163,14 +163,22 @@ int ft_digest(const void *buf, uint64_t nbytes, uint32_t block_bytes,
  *                block into L2; 0 = chosen per group.  When warps or
  *                l2_prefetch is set, every group takes that shape (warps 0
  *                then meaning 16, l2_prefetch 0 no prefetch).
- * ft_plan_tune reports the tile size, and a warps / l2_prefetch value only
- * when every group has it (0 when the groups differ; ft_plan_groups gives
- * each group's). */
+ *   kernels      1 = the whole batch as one persistent kernel whose warps take
+ *                the batch's tiles in turn whatever their element kind and R
+ *                (16 warps, no prefetch; warps must then be 0 or 16 and
+ *                l2_prefetch not 2); 2 = one kernel per group, the groups as
+ *                parallel branches of the graph; 0 = the faster of the two as
+ *                timed by the autotuner (one per group when warps or
+ *                l2_prefetch rule out the one-kernel shape).
+ * ft_plan_tune reports the tile size, the kernels choice, and a warps /
+ * l2_prefetch value only when every group has it (0 when the groups differ;
+ * ft_plan_groups gives each group's). */
 typedef struct ft_tune {
     int32_t tile_blocks;
     int32_t ctas_per_sm;
     int32_t warps;
     int32_t l2_prefetch;
+    int32_t kernels;
 } ft_tune;
 
 /* One (element kind, R) group of a plan and the launch shape it runs with. */
@@ -195,7 +203,8 @@ typedef struct ft_plan ft_plan;   /* library-owned */
  * which it overwrites: first the tile size, then each group's warps per CTA
  * and L2 prefetch in turn; the result is kept per batch signature for later
  * plans of the process.  It then captures one CUDA graph: the statistics
- * reset followed by the groups' persistent kernels as parallel branches.
+ * reset followed by the groups' persistent kernels as parallel branches, or
+ * by the one kernel for the whole batch (ft_tune.kernels).
  * The caller keeps every buffer alive and in place until ft_plan_destroy.
  * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
 int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks,

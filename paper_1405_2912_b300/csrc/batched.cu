@@ -128,6 +128,7 @@ void BatchLayout::build(const std::vector<TaskArgs> &in, int tile_blocks)
     groups.clear();
     tile_first.clear();
     tile_task.clear();
+    tile_first_global.clear();
     // order tasks by (kind, R), stable, so that each group is contiguous
     std::vector<int> order(in.size());
     for (size_t i = 0; i < in.size(); ++i) order[i] = (int)i;
@@ -137,6 +138,7 @@ void BatchLayout::build(const std::vector<TaskArgs> &in, int tile_blocks)
     user_index.assign(order.begin(), order.end());
     for (int idx : order) tasks.push_back(in[idx]);
     tile_first.resize(tasks.size());
+    tile_first_global.resize(tasks.size());
     for (size_t t = 0; t < tasks.size();) {
         GroupHost gh;
         gh.kind = tasks[t].kind;
@@ -149,6 +151,7 @@ void BatchLayout::build(const std::vector<TaskArgs> &in, int tile_blocks)
             const unsigned long long nblk = a.nfull + (a.tail_bytes ? 1 : 0);
             const unsigned long long nt = (nblk + tile_blocks - 1) / tile_blocks;
             tile_first[t] = g_tiles;
+            tile_first_global[t] = gh.tile0 + g_tiles;
             for (unsigned long long k = 0; k < nt; ++k) tile_task.push_back((uint32_t)t);
             g_tiles += nt;
             ++t;
@@ -162,7 +165,7 @@ void BatchLayout::build(const std::vector<TaskArgs> &in, int tile_blocks)
 size_t BatchLayout::device_bytes() const
 {
     return align(sizeof(TaskArgs) * tasks.size()) + align(8 * tile_first.size()) + align(4 * tile_task.size()) +
-           align(16 * groups.size());
+           align(8 * tile_first_global.size()) + align(16 * groups.size());
 }
 
 // Packs the layout into `host` (device_bytes() long) as it must appear at
@@ -176,10 +179,14 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
     off += align(8 * tile_first.size());
     const size_t o_map = off;
     off += align(4 * tile_task.size());
+    const size_t o_gfirst = off;
+    off += align(8 * tile_first_global.size());
     const size_t o_cnt = off;
     if (!tasks.empty()) std::memcpy(host + o_tasks, tasks.data(), sizeof(TaskArgs) * tasks.size());
     if (!tile_first.empty()) std::memcpy(host + o_first, tile_first.data(), 8 * tile_first.size());
     if (!tile_task.empty()) std::memcpy(host + o_map, tile_task.data(), 4 * tile_task.size());
+    if (!tile_first_global.empty())
+        std::memcpy(host + o_gfirst, tile_first_global.data(), 8 * tile_first_global.size());
     std::memset(host + o_cnt, 0, 16 * groups.size());   // tile counters, then done counters
     gd.clear();
     for (size_t i = 0; i < groups.size(); ++i) {
@@ -201,6 +208,13 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
     }
     counters_dev = reinterpret_cast<unsigned long long *>(dev + o_cnt);
     tasks_dev = reinterpret_cast<const TaskArgs *>(dev + o_tasks);
+    std::memset(&mixed, 0, sizeof(mixed));
+    mixed.tasks = tasks_dev;
+    mixed.tile_task = reinterpret_cast<const uint32_t *>(dev + o_map);
+    mixed.tile_first_global = reinterpret_cast<const unsigned long long *>(dev + o_gfirst);
+    mixed.total_tiles = tile_task.size();
+    mixed.counter = counters_dev;
+    mixed.tile_blocks = tile_blocks_;
 }
 
 int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s, int max_ctas)
@@ -231,6 +245,7 @@ struct ft_plan {
     size_t dev_bytes = 0;
     ft_tune tune{0, 0, 0, 0};
     std::map<std::pair<int, int>, std::pair<int, int>> shape;   // (kind, R) -> (warps, prefetch)
+    bool mixed = false;                      // the whole batch as one kernel (batched_mixed.cu)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
@@ -280,6 +295,7 @@ static int launch_batch_branches(ft_plan *p, cudaStream_t s)
 {
     const BatchLayout &L = p->layout;
     int rc = launch_batch_reset(L.tasks_dev, (int)L.tasks.size(), L.counters_dev, (int)p->gd.size(), s);
+    if (rc == FT_OK && p->mixed) return launch_mixed(L.mixed, p->tune.ctas_per_sm, s);
     if (rc != FT_OK || p->gd.size() <= 1) {
         for (const GroupDev &g : p->gd)
             if (rc == FT_OK) rc = launch_group(g, p->tune.ctas_per_sm, s);
@@ -344,6 +360,7 @@ static int build_exec(ft_plan *p, cudaGraph_t *graph, cudaGraphExec_t *exec, uns
 struct TuneResult {
     int tile_blocks;
     std::map<std::pair<int, int>, std::pair<int, int>> shape;
+    bool mixed;
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneResult> g_tune_cache;
@@ -413,9 +430,13 @@ static int time_replay(ft_plan *p, cudaStream_t s, float *best_ms)
 static int autotune(ft_plan *p, const ft_tune *forced, TuneResult *out)
 {
     const std::string key = signature(p->args);
-    const bool free_shape = !forced || (forced->warps == 0 && forced->l2_prefetch == 0);
+    const bool forced_mixed = forced && forced->kernels == 1;
+    // the one-kernel form runs 16 warps without prefetch: a caller's other shape rules it out
+    const bool mixed_allowed = !forced || ((forced->warps == 0 || forced->warps == 16) && forced->l2_prefetch != 2);
+    const bool free_kernels = (!forced || forced->kernels == 0) && mixed_allowed;
+    const bool free_shape = !forced_mixed && (!forced || (forced->warps == 0 && forced->l2_prefetch == 0));
     const bool free_tile = !forced || forced->tile_blocks == 0;
-    if (free_shape && free_tile) {
+    if (free_shape && free_tile && free_kernels) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
@@ -430,6 +451,8 @@ static int autotune(ft_plan *p, const ft_tune *forced, TuneResult *out)
     TuneResult best;
     best.tile_blocks = free_tile ? 8 : forced->tile_blocks;
     best.shape = p->shape;
+    best.mixed = forced_mixed;
+    p->mixed = forced_mixed;
     float best_ms = 1e30f;
     if (free_tile) {
         for (int tb : {1, 2, 4, 8, 16, 32}) {
@@ -465,10 +488,29 @@ static int autotune(ft_plan *p, const ft_tune *forced, TuneResult *out)
         }
         p->shape = best.shape;
     }
+    if (rc == FT_OK && free_kernels) {
+        // the whole batch as one kernel, against the best per-group graph
+        if (best_ms >= 1e29f && (rc = upload_layout(p, best.tile_blocks)) == FT_OK)
+            rc = time_replay(p, s, &best_ms);
+        p->mixed = true;
+        std::vector<int> tiles;
+        if (free_tile) tiles = {4, 8, 16};
+        else tiles = {best.tile_blocks};
+        for (size_t i = 0; i < tiles.size() && rc == FT_OK; ++i) {
+            float ms = 0;
+            if ((rc = upload_layout(p, tiles[i])) != FT_OK || (rc = time_replay(p, s, &ms)) != FT_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.tile_blocks = tiles[i];
+                best.mixed = true;
+            }
+        }
+        p->mixed = best.mixed;
+    }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (rc != FT_OK) return rc;
-    if (free_shape && free_tile) {
+    if (free_shape && free_tile && free_kernels) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
@@ -493,7 +535,8 @@ int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks, co
     if (tune && ((tune->tile_blocks && (tune->tile_blocks < 1 || tune->tile_blocks > 64)) ||
                  tune->ctas_per_sm < 0 || tune->ctas_per_sm > 8 ||
                  (tune->warps != 0 && tune->warps != 8 && tune->warps != 12 && tune->warps != 16) ||
-                 tune->l2_prefetch < 0 || tune->l2_prefetch > 2))
+                 tune->l2_prefetch < 0 || tune->l2_prefetch > 2 || tune->kernels < 0 || tune->kernels > 2 ||
+                 (tune->kernels == 1 && ((tune->warps != 0 && tune->warps != 16) || tune->l2_prefetch == 2))))
         return FT_EINVAL;
     ft_plan *p = new (std::nothrow) ft_plan();
     if (!p) return FT_ENOMEM;
@@ -508,19 +551,21 @@ int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks, co
     }
     if (tune) p->tune = *tune;
     p->tune.ctas_per_sm = tune ? tune->ctas_per_sm : 0;
-    const bool forced_shape = tune && (tune->warps != 0 || tune->l2_prefetch != 0);
+    const bool forced_shape = tune && (tune->warps != 0 || tune->l2_prefetch != 0 || tune->kernels == 1);
     if (forced_shape) {
         // the caller's shape for every group
         for (const TaskArgs &a : p->args)
             p->shape[{a.kind, a.R}] = {tune->warps ? tune->warps : kBatchWarps, tune->l2_prefetch == 2 ? 1 : 0};
     }
     int rc = FT_OK;
-    if (!tune || tune->tile_blocks == 0 || !forced_shape) {
+    p->mixed = tune && tune->kernels == 1;
+    if (!tune || tune->tile_blocks == 0 || !forced_shape || tune->kernels == 0) {
         TuneResult t;
         rc = autotune(p, tune, &t);
         if (rc == FT_OK) {
             p->tune.tile_blocks = t.tile_blocks;
             if (!forced_shape) p->shape = t.shape;
+            p->mixed = t.mixed;
         }
     }
     if (rc == FT_OK) rc = upload_layout(p, p->tune.tile_blocks);
@@ -534,6 +579,11 @@ int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks, co
         }
         p->tune.warps = w < 0 ? kBatchWarps : w;
         p->tune.l2_prefetch = pf < 0 ? 1 : pf;
+        if (p->mixed) {
+            p->tune.warps = kBatchWarps;
+            p->tune.l2_prefetch = 1;
+        }
+        p->tune.kernels = p->mixed ? 1 : 2;
     }
     if (rc == FT_OK) rc = capture(p);
     if (rc != FT_OK) {
@@ -555,8 +605,8 @@ int ft_plan_groups(const ft_plan *p, ft_plan_group *out, int32_t max, int32_t *n
         out[k].dtype = kDtypeOfKind[g.kind];
         out[k].R = g.R;
         out[k].tasks = gh.t1 - gh.t0;
-        out[k].warps = g.warps ? g.warps : ftv::kBatchWarps;
-        out[k].l2_prefetch = g.pf;
+        out[k].warps = p->mixed ? ftv::kBatchWarps : g.warps ? g.warps : ftv::kBatchWarps;
+        out[k].l2_prefetch = p->mixed ? 0 : g.pf;
         out[k].tile_blocks = g.tile_blocks;
         out[k].tiles = g.total_tiles;
     }
@@ -576,7 +626,13 @@ int ft_vote_batched(ft_plan *p, ft_stream stream)
 int ft_vote_batched_nograph(ft_plan *p, ft_stream stream)
 {
     if (!p) return FT_EINVAL;
-    return ftv::launch_batch(p->layout, p->gd, p->tune.ctas_per_sm, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->mixed) {
+        const ftv::BatchLayout &L = p->layout;
+        const int rc = ftv::launch_batch_reset(L.tasks_dev, (int)L.tasks.size(), L.counters_dev, (int)p->gd.size(), s);
+        return rc == FT_OK ? ftv::launch_mixed(L.mixed, p->tune.ctas_per_sm, s) : rc;
+    }
+    return ftv::launch_batch(p->layout, p->gd, p->tune.ctas_per_sm, s);
 }
 
 int ft_plan_tune(const ft_plan *p, ft_tune *out)

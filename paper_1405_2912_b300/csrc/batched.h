@@ -59,6 +59,20 @@ struct SmallGroup {
 };
 int launch_small_group(const SmallGroup &g, cudaStream_t s, int max_ctas = 0);
 
+// The whole batch as one persistent kernel (batched_mixed.cu): the tiles of
+// every group back to back (tile_task), and each task's first tile in that
+// sequence.  counter is zeroed before the launch.
+struct MixedDev {
+    const TaskArgs *tasks;
+    const uint32_t *tile_task;
+    const unsigned long long *tile_first_global;
+    unsigned long long total_tiles;
+    unsigned long long *counter;
+    int32_t tile_blocks;
+    int32_t pad_;
+};
+int launch_mixed(const MixedDev &g, int ctas_per_sm, cudaStream_t s);
+
 struct GroupHost {
     int kind, R;
     int t0, t1;                 // task range in the ordered table
@@ -72,10 +86,12 @@ struct BatchLayout {
     std::vector<GroupHost> groups;
     std::vector<unsigned long long> tile_first;   // per ordered task: first tile in its group
     std::vector<uint32_t> tile_task;              // per tile (all groups back to back)
+    std::vector<unsigned long long> tile_first_global;   // per ordered task: first tile in tile_task
     int tile_blocks_ = 8;
     // set by pack(): device addresses of the table and the counters
     const TaskArgs *tasks_dev = nullptr;
     unsigned long long *counters_dev = nullptr;
+    MixedDev mixed{};                             // the batch as one kernel (counter: counters_dev[0])
 
     static size_t align(size_t x) { return (x + 255) & ~size_t(255); }
     void build(const std::vector<TaskArgs> &in, int tile_blocks);

@@ -57,7 +57,7 @@ class ft_vote_desc(ctypes.Structure):
 
 class ft_tune(ctypes.Structure):
     _fields_ = [("tile_blocks", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("warps", ctypes.c_int32),
-                ("l2_prefetch", ctypes.c_int32)]
+                ("l2_prefetch", ctypes.c_int32), ("kernels", ctypes.c_int32)]
 
 
 class ft_plan_group(ctypes.Structure):

@@ -53,14 +53,17 @@ def _run(tasks, tune=None, graph=True, reps=1):
         fv.check(fv.ft_plan_groups(plan, None, 0, ctypes.byref(n)), "ft_plan_groups")
         groups = (fv.ft_plan_group * max(1, n.value))()
         fv.check(fv.ft_plan_groups(plan, groups, n.value, ctypes.byref(n)), "ft_plan_groups")
-        return (chosen.tile_blocks, chosen.ctas_per_sm, chosen.warps, chosen.l2_prefetch), list(groups)[:n.value]
+        return (chosen.tile_blocks, chosen.ctas_per_sm, chosen.warps, chosen.l2_prefetch, chosen.kernels), \
+            list(groups)[:n.value]
     finally:
         fv.ft_plan_destroy(plan)
 
 
 @pytest.mark.parametrize("tune,graph", [(None, True), ((1, 1), True), ((3, 0), False), ((64, 1), True),
                                         ((4, 0, 8, 2), True), ((2, 0, 12, 1), True), ((0, 0, 16, 2), False),
-                                        ((5, 0, 8, 1), False), ((7, 0, 12, 2), True), ((1, 0, 16, 1), True)])
+                                        ((5, 0, 8, 1), False), ((7, 0, 12, 2), True), ((1, 0, 16, 1), True),
+                                        ((4, 0, 0, 0, 1), True), ((0, 0, 0, 0, 1), False), ((1, 0, 16, 1, 1), True),
+                                        ((8, 0, 0, 0, 2), True), ((3, 0, 0, 0, 1), False)])
 def test_mixed_batch_matches_oracle(tune, graph):
     from paper_1405_2912_b300 import ftvote as fv
     specs = _mixed_specs()
@@ -74,11 +77,14 @@ def test_mixed_batch_matches_oracle(tune, graph):
     assert sum(g.tasks for g in groups) == len(tasks)
     kinds = [(g.dtype, g.R) for g in groups]
     assert len(set(kinds)) == len(kinds)
+    assert chosen[4] in (1, 2)
+    if tune is not None and len(tune) > 4:
+        assert chosen[4] == tune[4]
     for g in groups:
         assert g.warps in (8, 12, 16) and g.l2_prefetch in (0, 1) and g.tile_blocks == chosen[0]
-        if tune is not None and len(tune) > 2:
+        if tune is not None and len(tune) > 2 and (tune[2] or tune[3]):
             assert g.warps == (tune[2] or 16) and g.l2_prefetch == (1 if tune[3] == 2 else 0)
-    if tune is not None and len(tune) > 2:
+    if tune is not None and len(tune) > 2 and (tune[2] or tune[3]):
         assert chosen[2] == (tune[2] or 16) and chosen[3] == (2 if tune[3] == 2 else 1)
     for p, tk in zip(probs, tasks):
         assert_same(tk.result(), oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
@@ -89,7 +95,8 @@ def test_plan_rejects_bad_tune():
     p = synth.task_problem(synth.TaskSpec(100, "f32", 3, False, 1))
     tk = DevTask(p)
     plan = ctypes.c_void_p()
-    for bad in ((65, 0, 0, 0), (1, 9, 0, 0), (1, 0, 10, 0), (1, 0, 0, 3), (1, 0, -1, 0)):
+    for bad in ((65, 0, 0, 0), (1, 9, 0, 0), (1, 0, 10, 0), (1, 0, 0, 3), (1, 0, -1, 0), (1, 0, 0, 0, 3),
+                (1, 0, 8, 0, 1), (1, 0, 0, 2, 1)):
         t = fv.ft_tune(*bad)
         assert fv.ft_plan_create(ctypes.byref(plan), desc_array([tk]), 1, ctypes.byref(t)) == fv.FT_EINVAL, bad
 
