@@ -50,7 +50,9 @@ static __device__ __noinline__ void copy_out_if_last(const CopyOut &c)
         *c.counter = 0;
         *c.done_ctas = 0;
     }
-    __threadfence_system();
+    // no system-scope fence: the host reads stats_out only once the event
+    // recorded after the batch's kernels has completed, which makes the
+    // kernel's writes to host memory visible to it
 }
 
 // The task of a tile: from the tile map (plans and large batches) ...

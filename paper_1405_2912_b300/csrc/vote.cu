@@ -276,7 +276,10 @@ __device__ __noinline__ void slot_finish(const SlotRef &sr, ft_stats *user)
     __syncthreads();
     if (threadIdx.x == 0) {
         sr.slot->done = 0;
-        __threadfence_system();
+        // the slot's reset values are visible on the device before the free
+        // flag is written, so the vote the host launches on the slot once it
+        // reads the flag sees them; only the GPU reads the slot
+        __threadfence();
         *reinterpret_cast<volatile unsigned int *>(sr.busy) = 0u;
     }
 }
