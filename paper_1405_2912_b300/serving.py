@@ -71,11 +71,14 @@ def _replay(srv, descs, arrivals_s, payload_of, start_delay_us):
             head += nd.value
     done_at = np.array([results[k].done_us for k in range(n)], dtype=np.float64)
     submit_at = np.array([results[k].submit_us for k in range(n)], dtype=np.float64)
+    launch_at = np.array([results[k].launch_us for k in range(n)], dtype=np.float64)
+    launched_at = np.array([results[k].launched_us for k in range(n)], dtype=np.float64)
     errors = sum(1 for k in range(n) if results[k].status != fv.FT_OK)
     lat = done_at - arr
     span_s = (done_at.max() - arr.min()) / 1e6 if n else 0.0
     return {"latency_us": lat, "submit_lag_us": submit_at - arr, "server_us": done_at - submit_at,
-            "refused": refused, "span_s": span_s, "errors": errors}
+            "queue_us": launch_at - submit_at, "launch_us": launched_at - launch_at,
+            "device_us": done_at - launched_at, "refused": refused, "span_s": span_s, "errors": errors}
 
 
 def summarize(r, bytes_per_req):
