@@ -66,6 +66,7 @@ struct CrcTables {
     uint32_t shift4096[8][16];  // shift4096[p][v] = (v << 4p) * x^(8*4096)
     uint32_t init4096;          // 0xFFFFFFFF * x^(8*4096): initial-value term of a full block
     uint32_t shift_pow[32][8][16];   // shift_pow[j][p][v] = (v << 4p) * x^(8 * 2^j)
+    uint32_t shift1552[8][16];       // shift1552[p][v] = (v << 4p) * x^(8*1552): a lane's last four vectors
 };
 
 constexpr CrcTables make_crc_tables()
@@ -104,6 +105,11 @@ constexpr CrcTables make_crc_tables()
         for (int p = 0; p < 8; ++p)
             for (uint32_t v = 0; v < 16; ++v) t.shift4096[p][v] = gf_mul(v << (4 * p), K);
         t.init4096 = gf_mul(0xFFFFFFFFu, K);
+    }
+    {
+        const uint32_t K = gf_xpow8(16 + 3 * 512);
+        for (int p = 0; p < 8; ++p)
+            for (uint32_t v = 0; v < 16; ++v) t.shift1552[p][v] = gf_mul(v << (4 * p), K);
     }
     {
         uint32_t K = gf_xpow8(1);                   // x^8, then squared: x^(8 * 2^j)
@@ -280,6 +286,18 @@ __device__ __forceinline__ uint32_t shift_bytes(uint32_t c, uint32_t k)
         c = r;
     }
     return c;
+}
+
+// Multiply by x^(8*1552), the span from the start of a lane's fifth vector to
+// the end of its eighth (one vector and three jumps of 512 bytes): a lane's
+// register over its first four vectors, moved to where the register over its
+// last four ends.
+__device__ __forceinline__ uint32_t shift_1552(uint32_t c)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) r ^= g_crc.shift1552[p][(c >> (4 * p)) & 15u];
+    return r;
 }
 
 // Multiply by x^(8*4096) with the shared nibble tables (uniform across the warp).
@@ -834,7 +852,14 @@ __device__ __forceinline__ const uint8_t *rep_for_lane(const TaskArgs &a, int la
 // measured 9 % slower on 3 x 256M f32: the table lookups then sit between the
 // vote and the next loads.
 // ---------------------------------------------------------------------------
-template <int K, int R, int JB = kSubBatch<K, R>>
+//
+// SMALL (the shape of votes of at most one block per warp, where each warp's
+// one block is the whole critical path): the lane's CRC runs as two
+// independent chains, over vectors 0-3 while the loads of the later vectors
+// are in flight and over vectors 4-7 at the end, joined by one multiplication
+// (shift_1552); and the R = 3 closed form keeps its pairwise masks in
+// registers instead of reading a flagged sub-batch again.
+template <int K, int R, int JB = kSubBatch<K, R>, bool SMALL = false>
 __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long long b, unsigned long long b_next,
                                                 const uint32_t *s_crc, const CrcLane &L, LaneStats<R> &st, int lane)
 {
@@ -848,9 +873,15 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     const typename E::Ctx ctx = E::ctx(a.abs_tol, a.rel_tol);
     const unsigned long long boff = b * kBlockBytes;
     if (lane < R && b_next < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + b_next * kBlockBytes, kBlockBytes);
-    constexpr bool kOverlap = VotePolicy<K, R>::kOverlapCrc;
+    constexpr bool kOverlap = SMALL || VotePolicy<K, R>::kOverlapCrc;
+    constexpr bool kInlineStats = SMALL && F == F_CLOSED3 && K != K_B1;
     uint4 yall[8];            // the lane's voted vectors l + 32 t, t = 0..7
-    uint32_t cc = 0;          // the lane's CRC register
+    uint32_t cc = 0;          // the lane's CRC register (over vectors 0-3 when SMALL)
+    uint32_t cc2 = 0;         // SMALL: the register over vectors 4-7
+    auto digest = [&](int t) {
+        if (!SMALL || t < 4) cc = crc_vec(s_crc, L, cc, yall[t], t == 7);
+        else cc2 = crc_vec(s_crc, L, cc2, yall[t], t == 7);
+    };
 
 #pragma unroll
     for (int j0 = 0; j0 < 8; j0 += JB) {
@@ -864,16 +895,31 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
             // digest the previous sub-batch while these loads are in flight
             if (j0 > 0) {
 #pragma unroll
-                for (int jj = 0; jj < JB; ++jj) cc = crc_vec(s_crc, L, cc, yall[j0 - JB + jj], j0 - JB + jj == 7);
+                for (int jj = 0; jj < JB; ++jj) digest(j0 - JB + jj);
             }
         }
         uint64_t flagged = 0;
+        uint64_t n01 = 0, n02 = 0, n12 = 0;   // kInlineStats: bit k set where a pair of element k differs
         const unsigned long long idx0 = b * kEpb + (unsigned long long)(lane + 32 * j0) * kPerVec;
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
             uint4 yv = v[0][jj];
             if constexpr (K == K_B1 && R == 3) {
                 yv = vote_b1_closed3(v[0][jj], v[1][jj], v[2][jj], flagged);
+            } else if constexpr (kInlineStats) {
+#pragma unroll
+                for (int e = 0; e < kPerVec; ++e) {
+                    const typename E::P p0 = E::prep(E::get(v[0][jj], e), ctx), p1 = E::prep(E::get(v[1][jj], e), ctx),
+                                        p2 = E::prep(E::get(v[2][jj], e), ctx);
+                    const bool e01 = E::eq(p0, p1, ctx), e02 = E::eq(p0, p2, ctx), e12 = E::eq(p1, p2, ctx);
+                    const bool w1 = e12 & !e02;
+                    const bool w2 = e02 & e12 & !e01;
+                    E::set(yv, e, w2 ? E::get(v[2][jj], e) : (w1 ? E::get(v[1][jj], e) : E::get(v[0][jj], e)));
+                    const uint64_t bit = 1ull << (jj * kPerVec + e);
+                    n01 |= e01 ? 0ull : bit;
+                    n02 |= e02 ? 0ull : bit;
+                    n12 |= e12 ? 0ull : bit;
+                }
             } else {
                 // kinds compared bits first (all but f32): a vector equal in
                 // all replicas is replica 0's, with no mismatch
@@ -904,8 +950,11 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
         }
         if constexpr (F == F_CLOSED2)
             if (flagged) closed2_stats<kPerVec>(flagged, idx0, st);
-        if constexpr (F == F_CLOSED3)
+        if constexpr (kInlineStats) {
+            if (n01 | n02 | n12) closed3_stats<kPerVec>(n01, n02, n12, idx0, st);
+        } else if constexpr (F == F_CLOSED3) {
             if (flagged) closed3_rare<K, JB>(a, boff, lane, j0, idx0, st);
+        }
         if constexpr (F == F_EQ0) {
             if (flagged) {
                 // re-voted in the exact form and stored; the lane reads its
@@ -919,11 +968,12 @@ __device__ __forceinline__ void vote_full_block(const TaskArgs &a, unsigned long
     }
     if constexpr (kOverlap) {
 #pragma unroll
-        for (int jj = 0; jj < JB; ++jj) cc = crc_vec(s_crc, L, cc, yall[8 - JB + jj], 8 - JB + jj == 7);
+        for (int jj = 0; jj < JB; ++jj) digest(8 - JB + jj);
     } else {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) cc = crc_vec(s_crc, L, cc, yall[t], t == 7);
+        for (int t = 0; t < 8; ++t) digest(t);
     }
+    if constexpr (SMALL) cc = shift_1552(cc) ^ cc2;
     const uint32_t raw = crc_combine(s_crc, cc, lane);
     if (lane == 0 && a.crc) a.crc[b] = ~(raw ^ g_crc.init4096);
 }

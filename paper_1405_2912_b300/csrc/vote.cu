@@ -300,7 +300,7 @@ __device__ __noinline__ void slot_finish(const SlotRef &sr, ft_stats *user)
 // caller ran before; without one it is the statistics reset, which touches
 // only the statistics, and the wait moves to just before they are added.
 // ---------------------------------------------------------------------------
-template <int K, int R, int W, bool PF, int JB>
+template <int K, int R, int W, bool PF, int JB, bool SMALL>
 __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a, const SlotRef sr)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a, const
     LaneStats<R> st;
     st.init();
     for (unsigned long long b = gw; b < a.nfull; b += step)
-        vote_full_block<K, R, JB>(a, b, PF ? b + step : ~0ull, s_crc, L, st, lane);
+        vote_full_block<K, R, JB, SMALL>(a, b, PF ? b + step : ~0ull, s_crc, L, st, lane);
     if (a.tail_bytes && a.nfull % step == gw) {
         // the partial last block goes to the warp whose turn it would be
         LaneStats<R> ts;
@@ -340,10 +340,10 @@ __global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a, const
 
 // Launches one shape.  With a slot the statistics reset is not needed; the
 // kernel is a programmatic dependent of the caller's previous kernel.
-template <int K, int R, int kVoteWarps, bool PF, int JB>
+template <int K, int R, int kVoteWarps, bool PF, int JB, bool SMALL = false>
 static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, const SlotRef &sr)
 {
-    auto fn = vote_kernel<K, R, kVoteWarps, PF, JB>;
+    auto fn = vote_kernel<K, R, kVoteWarps, PF, JB, SMALL>;
     const size_t smem = kSmemBytes;
     int sms = 0, per_sm = 0;
     int rc = occupancy(reinterpret_cast<const void *>(fn), kVoteWarps * 32, smem, &sms, &per_sm);
@@ -376,7 +376,9 @@ static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch
 // against 20 us; equal at 3 x 64M; 6.7 against 6.25 TB/s the other way at
 // 3 x 256M).  Votes of at most one block per warp of a full wave of 8-warp
 // CTAs (1184 blocks, 4.6 MiB of output) take 8-warp CTAs, which spreads them
-// over up to all 148 SMs instead of the 74 that 16-warp CTAs would use.
+// over up to all 148 SMs instead of the 74 that 16-warp CTAs would use, and
+// the SMALL form of the block voter (two CRC chains per lane, R = 3 pairwise
+// masks kept in registers).
 constexpr unsigned long long kSmallVoteBlocks = 32768;
 constexpr int kTinyWarps = 8;
 
@@ -398,11 +400,11 @@ static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *c
         if (w == 12) return launch_vote_shape<K, R, 12, true, JB>(a, s, cfg, sr);
     }
     int sms = 0, per_sm = 0;
-    int rc = occupancy(reinterpret_cast<const void *>(vote_kernel<K, R, kTinyWarps, false, JB>), kTinyWarps * 32,
-                       kSmemBytes, &sms, &per_sm);
+    int rc = occupancy(reinterpret_cast<const void *>(vote_kernel<K, R, kTinyWarps, false, JB, true>),
+                       kTinyWarps * 32, kSmemBytes, &sms, &per_sm);
     if (rc != FT_OK) return rc;
     if (nblk <= (unsigned long long)sms * per_sm * kTinyWarps)
-        return launch_vote_shape<K, R, kTinyWarps, false, JB>(a, s, cfg, sr);
+        return launch_vote_shape<K, R, kTinyWarps, false, JB, true>(a, s, cfg, sr);
     if constexpr (P::kPrefetch) {
         if (nblk <= kSmallVoteBlocks) return launch_vote_shape<K, R, 16, false, JB>(a, s, cfg, sr);
     }
