@@ -89,7 +89,7 @@ struct ScanLookup {
 // STATIC: warp w of the grid takes tiles w, w + (warps in the grid), ...
 // instead of claiming them, which saves a round trip to the counter per tile
 // where the tiles are too few for their sizes to need balancing.
-template <int K, int R, bool PF, bool STATIC, class Lookup>
+template <int K, int R, bool PF, bool STATIC, class Lookup, bool SMALL = false>
 __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long *counter, unsigned long long total_tiles,
                                            int tile_blocks, const uint32_t *s_crc)
 {
@@ -124,7 +124,8 @@ __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long 
         const unsigned long long b0 = k * (unsigned long long)tile_blocks;
         const unsigned long long b1 = min(b0 + (unsigned long long)tile_blocks, a.nfull);
         for (unsigned long long b = b0; b < b1; ++b)
-            vote_full_block<K, R>(a, b, (PF && b + 1 < b1) ? b + 1 : ~0ull, s_crc, L, st, lane);
+            vote_full_block<K, R, kSubBatch<K, R>, SMALL>(a, b, (PF && b + 1 < b1) ? b + 1 : ~0ull, s_crc, L, st,
+                                                          lane);
         if (a.tail_bytes && a.nfull / tile_blocks == k) {
             LaneStats<R> ts;
             ts.init();
@@ -172,7 +173,9 @@ __global__ void __launch_bounds__(W * 32, 1) batched_small_kernel(const __grid_c
     }
     load_crc_tables<W>(s_crc);
     __syncthreads();
-    vote_tiles<K, R, false, true>(lk, g.counter, g.total_tiles, g.tile_blocks, s_crc);
+    // the 8-warp instance serves groups of at most a few tiles per warp: the
+    // SMALL block form (see vote_full_block)
+    vote_tiles<K, R, false, true, ScanLookup, W == 8>(lk, g.counter, g.total_tiles, g.tile_blocks, s_crc);
     copy_out_if_last(CopyOut{g.done_ctas, g.counter, g.tasks, g.ntasks, true, g.stats_base, g.stats_out});
 }
 

@@ -18,6 +18,7 @@ struct VoteLaunch {
     int warps;         // warps per CTA (f32 R = 3: 4, 8 or 16; other kinds: the shapes built for them)
     int sub_batch;     // 16-byte vectors per lane per sub-batch (f32 R = 3: 4 or 8)
     int stats_mode;    // 1 = statistics reset kernel + voter, 2 = one kernel with a statistics slot
+    int small_form;    // votes of 1185..32768 blocks: 1 = 16 warps with the SMALL block form, 2 = without
 };
 
 extern std::atomic<unsigned long long> g_launches;

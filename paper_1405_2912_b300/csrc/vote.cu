@@ -381,6 +381,11 @@ static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch
 // masks kept in registers).
 constexpr unsigned long long kSmallVoteBlocks = 32768;
 constexpr int kTinyWarps = 8;
+// Up to 4096 blocks (16 MiB of output) the 16-warp shape also takes the SMALL
+// block form: f32 R = 3 3 x 2M 13.1 -> 10.7 us, 3 x 4M 18.6 -> 16.9 us;
+// from 16384 blocks on it no longer gains (3 x 16M 48.2 against 48.5 us, 5 x 8M
+// f64 76.6 against 75.3, 5 x 8M i32 43.1 against 42.9).
+constexpr unsigned long long kSmallFormBlocks = 4096;
 
 template <int K, int R>
 static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, const SlotRef &sr)
@@ -405,6 +410,11 @@ static int launch_vote_kr(const TaskArgs &a, cudaStream_t s, const VoteLaunch *c
     if (rc != FT_OK) return rc;
     if (nblk <= (unsigned long long)sms * per_sm * kTinyWarps)
         return launch_vote_shape<K, R, kTinyWarps, false, JB, true>(a, s, cfg, sr);
+    if (cfg && nblk <= kSmallVoteBlocks) {
+        if (cfg->small_form == 1) return launch_vote_shape<K, R, 16, false, JB, true>(a, s, cfg, sr);
+        if (cfg->small_form == 2) return launch_vote_shape<K, R, 16, false, JB, false>(a, s, cfg, sr);
+    }
+    if (nblk <= kSmallFormBlocks) return launch_vote_shape<K, R, 16, false, JB, true>(a, s, cfg, sr);
     if constexpr (P::kPrefetch) {
         if (nblk <= kSmallVoteBlocks) return launch_vote_shape<K, R, 16, false, JB>(a, s, cfg, sr);
     }
