@@ -225,6 +225,7 @@ static SlotPool *slot_pool(int dev)
     if (e == cudaSuccess) {
         std::memset(p.busy, 0, sizeof(unsigned int) * kSlots);
         init_slots_kernel<<<(kSlots + 255) / 256, 256, 0, st>>>(p.dev, kSlots);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

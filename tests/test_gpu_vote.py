@@ -4,6 +4,8 @@ CRC32C, per-replica mismatch counts and first indices, no-majority count and
 first index.  Sizes span many 4 KiB blocks and ragged tails; the workloads are
 the seeded generators of the five voter workloads, scaled down, plus the full
 256M-element f32 workload in the launch configuration that bench.py times."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -267,3 +269,53 @@ def test_dense_disagreement_other_r(dtype, R):
         if n > 1000:
             assert ref["no_majority"] > 0 and max(ref["mismatch"]) > 0
         assert_same(gpu_vote(reps, dtype, *tol), ref, R)
+
+
+def test_more_votes_in_flight_than_statistics_slots():
+    """ft_vote gathers a vote's statistics in one of 1024 library slots per
+    device and falls back to a statistics reset kernel when all are taken.
+    With four streams each held by a sleeping kernel, 1400 votes are queued
+    behind them (more than 1024 in flight at once), each into its own
+    statistics buffer: some take the fallback, every one equals the oracle,
+    and once they are done the slots serve new votes again."""
+    import torch
+    from paper_1405_2912_b300 import ftvote as fv
+    p = synth.cfg1(n=5000, flips=20)
+    ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+    dev = [torch.from_numpy(r).cuda() for r in p.replicas]
+    nstreams, per = 4, 350
+    k = nstreams * per
+    outs = [torch.empty_like(dev[0]) for _ in range(nstreams)]
+    crcs = [torch.empty(fv.n_blocks(4 * p.n), dtype=torch.int32, device="cuda") for _ in range(nstreams)]
+    stats = torch.full((k, 18), 7, dtype=torch.int64, device="cuda")
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    descs = [fv.make_desc(dev, outs[j], crcs[j], stats[0], p.abs_tol, p.rel_tol) for j in range(nstreams)]
+    fv.check(fv.ft_vote(ctypes.byref(descs[0]), fv.stream_handle(streams[0])), "ft_vote")   # sets up the pool
+    torch.cuda.synchronize()
+    for st_ in streams:
+        with torch.cuda.stream(st_):
+            torch.cuda._sleep(400_000_000)
+    l0 = fv.ft_launch_count()
+    for i in range(k):
+        j = i % nstreams
+        descs[j].stats = stats[i].data_ptr()
+        fv.check(fv.ft_vote(ctypes.byref(descs[j]), fv.stream_handle(streams[j])), "ft_vote")
+    # a vote through a slot is one launch, one past the pool two (reset and voter)
+    fell_back = fv.ft_launch_count() - l0 - k
+    torch.cuda.synchronize()
+    want = ([int(x) for x in ref["mismatch"]] + [0] * 5 + [int(x) for x in ref["first_mismatch"]] + [-1] * 5 +
+            [ref["no_majority"], ref["first_no_majority"]])
+    got = stats.cpu().numpy()
+    bad = [i for i in range(k) if list(got[i]) != want]
+    assert not bad, (len(bad), bad[:5])
+    for j in range(nstreams):
+        assert outs[j].cpu().numpy().tobytes() == ref["out"].tobytes()
+        assert np.array_equal(crcs[j].cpu().numpy().view(np.uint32), ref["block_crc"])
+    assert fell_back > 0, fell_back
+    stats.fill_(7)
+    for i in range(50):
+        descs[0].stats = stats[i].data_ptr()
+        fv.check(fv.ft_vote(ctypes.byref(descs[0]), fv.stream_handle(streams[0])), "ft_vote")
+    torch.cuda.synchronize()
+    got = stats[:50].cpu().numpy()
+    assert all(list(got[i]) == want for i in range(50))
