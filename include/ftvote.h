@@ -287,6 +287,12 @@ typedef struct ft_server_config {
                                    after its last batch before it sleeps until the next request;
                                    a request that finds it asleep waits for a thread wake-up
                                    (tens of microseconds): 0 = 2000, -1 = do not poll */
+    int32_t  size_ratio;        /* while another slot is free, a batch takes a waiting request only
+                                   if its bytes are within this factor of the batch's first
+                                   request's (a much smaller one would wait for the large one it
+                                   is packed with); on the last free slot everything waiting is
+                                   packed: 0 = 8, -1 = no limit, else 2 or more */
+    int32_t  pad_;
 } ft_server_config;
 
 typedef struct ft_result {

@@ -74,7 +74,9 @@ class ft_server_config(ctypes.Structure):
                 ("max_inflight", ctypes.c_int32),
                 ("max_batch_bytes", ctypes.c_uint64),
                 ("reserved_sms", ctypes.c_int32),
-                ("idle_spin_us", ctypes.c_int32)]
+                ("idle_spin_us", ctypes.c_int32),
+                ("size_ratio", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class ft_result(ctypes.Structure):

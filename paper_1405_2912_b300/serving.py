@@ -77,7 +77,7 @@ def _replay(srv, descs, arrivals_s, payload_of, start_delay_us):
     lat = done_at - arr
     span_s = (done_at.max() - arr.min()) / 1e6 if n else 0.0
     return {"latency_us": lat, "submit_lag_us": submit_at - arr, "server_us": done_at - submit_at,
-            "queue_us": launch_at - submit_at, "launch_us": launched_at - launch_at,
+            "queue_us": launch_at - submit_at, "launch_us": launched_at - launch_at, "launch_stamp": launch_at,
             "device_us": done_at - launched_at, "refused": refused, "span_s": span_s, "errors": errors}
 
 

@@ -17,9 +17,10 @@ from _gpu import DevTask, assert_same
 pytestmark = pytest.mark.gpu
 
 
-def _server(budget, max_slots=16, streams=2, tile=8, max_inflight=0):
+def _server(budget, max_slots=16, streams=2, tile=8, max_inflight=0, size_ratio=0):
     from paper_1405_2912_b300 import ftvote as fv
     cfg = fv.ft_server_config(budget, max_slots, streams, tile, max_inflight)
+    cfg.size_ratio = size_ratio
     srv = ctypes.c_void_p()
     fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
     return srv
@@ -150,7 +151,8 @@ def test_server_counters():
     from paper_1405_2912_b300 import ftvote as fv
     probs = _requests(k=12, seed=8)
     tasks = [DevTask(p) for p in probs]
-    srv = _server(budget=1 << 34, max_slots=4, streams=2)
+    # no size rule: the 12 requests are packed four by four whatever their sizes
+    srv = _server(budget=1 << 34, max_slots=4, streams=2, size_ratio=-1)
     try:
         fv.ft_server_pause(srv, 1)
         tks = []
@@ -427,3 +429,38 @@ def test_every_kind_and_r_through_the_server(user_stats):
         assert info.batches >= 4      # 49 requests, at most 16 per batch
     finally:
         fv.ft_server_destroy(srv)
+
+
+def test_size_rule_keeps_small_requests_out_of_a_large_ones_batch():
+    """With a slot to spare, a batch takes waiting requests only within the
+    size factor of its first one: a large request and small ones queued behind
+    it go into separate batches, and every result equals the oracle."""
+    from paper_1405_2912_b300 import ftvote as fv
+    big = synth.task_problem(synth.TaskSpec(1 << 20, "f32", 3, True, 31), config_id=5)
+    small = [synth.task_problem(synth.TaskSpec(3000 + 17 * i, "f32", 3, i % 2 == 0, 40 + i), config_id=5)
+             for i in range(5)]
+    probs = [big] + small
+    tasks = [DevTask(p) for p in probs]
+    srv = _server(budget=1 << 34, max_slots=16, streams=3)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tks = []
+        for t in tasks:
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(t.desc), ctypes.byref(tk)) == fv.FT_OK
+            tks.append(tk.value)
+        fv.ft_server_pause(srv, 0)
+        r = fv.ft_result()
+        launch = []
+        for tk in tks:
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+            launch.append(r.launch_us)
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        # the large request alone, the five small ones together
+        assert info.batches == 2
+        assert launch[0] != launch[1] and len(set(launch[1:])) == 1
+    finally:
+        fv.ft_server_destroy(srv)
+    for p, t in zip(probs, tasks):
+        assert_same(t.result(), oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
