@@ -19,6 +19,7 @@ struct VoteLaunch {
     int sub_batch;     // 16-byte vectors per lane per sub-batch (f32 R = 3: 4 or 8)
     int stats_mode;    // 1 = statistics reset kernel + voter, 2 = one kernel with a statistics slot
     int small_form;    // votes of 1185..32768 blocks: 1 = 16 warps with the SMALL block form, 2 = without
+    int max_ctas;      // 0 = no cap beyond the occupancy limit
 };
 
 extern std::atomic<unsigned long long> g_launches;
@@ -32,6 +33,12 @@ int dtype_kind(int dtype);
 int validate_desc(const ft_vote_desc *d);
 TaskArgs make_task_args(const ft_vote_desc *d);
 int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
+// The single-task voter on an already validated task, through a statistics
+// slot (one launch, programmatic dependent of the stream's previous kernel):
+// the slot is copied to a.stats at the end.  FT_EAGAIN, with nothing
+// launched, for an empty task or when every slot is taken.  Not for a stream
+// that is being captured.
+int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg);
 
 // One (element kind, R) group of a batch, as the batched kernel sees it.
 // tasks[t] for t in [t0, t1) belong to the group; the group's work is split

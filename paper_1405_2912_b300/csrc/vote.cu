@@ -352,7 +352,8 @@ static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < per_sm) per_sm = cfg->ctas_per_sm;
     const unsigned long long nblk = a.nfull + (a.tail_bytes ? 1 : 0);
     unsigned long long grid = (nblk + kVoteWarps - 1) / kVoteWarps;
-    const unsigned long long cap = (unsigned long long)sms * per_sm;
+    unsigned long long cap = (unsigned long long)sms * per_sm;
+    if (cfg && cfg->max_ctas > 0 && (unsigned long long)cfg->max_ctas < cap) cap = cfg->max_ctas;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     cudaLaunchConfig_t lc = {};
@@ -449,6 +450,20 @@ static int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg,
     case K_B8: return launch_vote_k<K_B8>(a, s, cfg, sr);
     default: return FT_EINVAL;
     }
+}
+
+int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
+{
+    if (a.n == 0) return FT_EAGAIN;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    SlotPool *pool = slot_pool(dev);
+    const int i = pool ? acquire_slot(*pool) : -1;
+    if (i < 0) return FT_EAGAIN;
+    const int rc = launch_vote(a, s, cfg, SlotRef{pool->dev + i, pool->busy_dev + i, 1});
+    if (rc != FT_OK) release_slot(*pool, i);
+    return rc;
 }
 
 int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)
