@@ -213,10 +213,12 @@ int ft_plan_create(ft_plan **plan, const ft_vote_desc *tasks, int32_t ntasks,
 /* Replay the plan's graph on `stream`: every task of the plan is voted. */
 int ft_vote_batched(ft_plan *plan, ft_stream stream);
 
-/* Launch the batched kernel without the graph (same work, two launches). */
+/* Launch the plan's kernels without the graph (same work: the statistics
+ * reset, then the group kernels one after another on `stream`, or the one
+ * kernel for the whole batch). */
 int ft_vote_batched_nograph(ft_plan *plan, ft_stream stream);
 
-/* Vote n tasks with one ft_vote each (two launches per task, in order, on
+/* Vote n tasks with one ft_vote each (one launch per task, in order, on
  * `stream`): the unbatched form that the batched plan is measured against. */
 int ft_vote_many(const ft_vote_desc *descs, int32_t n, ft_stream stream);
 

@@ -407,7 +407,7 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
 // variable, unless the configuration says otherwise: a request that arrives
 // within it is picked up without a wake-up.  A wake-up measured 50 to 70 us
 // on the GPU host; at 20k requests/s (Poisson) 2 % of the gaps between
-// requests exceed 200 us, about none 2 ms.
+// requests exceed 200 us, and practically none exceed 2 ms.
 constexpr double kSpinUs = 2000.0;
 
 // Requests of a batch stay within this factor of the batch's first request's
