@@ -50,6 +50,11 @@ struct SmallGroup {
     unsigned long long *done_ctas;
     const ft_stats *stats_base;      // the slot's statistics array (device)
     ft_stats *stats_out;             // its host-mapped copy
+    // per-task completion as GroupDev's (flag_out set); the task's last warp
+    // also puts its statistics and tiles_done entry back to their initial values
+    unsigned long long *tiles_done;
+    unsigned long long *flag_out;
+    unsigned long long seq;
     int32_t ntasks;
     int32_t tile_blocks;
     int32_t kind;

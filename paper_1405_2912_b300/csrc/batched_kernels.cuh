@@ -55,12 +55,63 @@ static __device__ __noinline__ void copy_out_if_last(const CopyOut &c)
     // kernel's writes to host memory visible to it
 }
 
+// Completion of each task on its own (the server, flag_out set): the warp
+// whose tiles complete a task copies the task's statistics to stats_out[i]
+// and then writes seq to flag_out[i], both host-mapped, i = the task's index
+// in the statistics array.  The host then sees the request done while the rest
+// of its batch is still voting.  tiles_done[i] is zero at launch; with
+// `reset`, the last warp puts it and the statistics back to their initial
+// values for the next launch.
+struct TaskDone {
+    unsigned long long *tiles_done;
+    const ft_stats *stats_base;
+    ft_stats *stats_out;
+    unsigned long long *flag_out;   // nullptr: off
+    unsigned long long seq;
+    bool reset;
+};
+
+// Called by every lane of a warp after it has flushed its statistics of the
+// task whose statistics are `stats`: adds the warp's `tiles` of the task to
+// its count and, if that completes the task's `need` tiles, hands it off.
+static __device__ __noinline__ void finish_task(const TaskDone &d, ft_stats *stats, unsigned long long tiles,
+                                                unsigned long long need, int lane)
+{
+    const size_t i = (size_t)(stats - d.stats_base);
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();   // lane 0 made the statistics atomics of the flush
+        last = atomicAdd(d.tiles_done + i, tiles) + tiles == need;
+    }
+    if (!__shfl_sync(0xFFFFFFFFu, last, 0)) return;
+    // every other warp that voted tiles of the task counted them after its
+    // own flush: their statistics are final in L2
+    __threadfence();
+    constexpr int kWords = (int)(sizeof(ft_stats) / 8);
+    if (lane < kWords) {
+        unsigned long long *w = reinterpret_cast<unsigned long long *>(stats) + lane;
+        reinterpret_cast<unsigned long long *>(d.stats_out + i)[lane] = __ldcg(w);
+        if (d.reset) *w = (lane < FT_MAX_R || lane == 2 * FT_MAX_R) ? 0ull : ~0ull;
+    }
+    if (lane == 0 && d.reset) d.tiles_done[i] = 0;
+    // each lane's writes reach the host (and the resets the device) before the flag
+    __threadfence_system();
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile unsigned long long *>(d.flag_out + i) = d.seq;
+}
+
 // The task of a tile: from the tile map (plans and large batches) ...
 struct MapLookup {
     const TaskArgs *tasks;
     const uint32_t *tile_task;
     const unsigned long long *tile_first;
+    int t_end;                       // one past the group's last task
+    unsigned long long total;        // the group's tiles
     __device__ __forceinline__ int task_of(unsigned long long tg, int) const { return (int)tile_task[tg]; }
+    __device__ __forceinline__ unsigned long long tiles_of(int t) const
+    {
+        return (t + 1 < t_end ? tile_first[t + 1] : total) - tile_first[t];
+    }
 };
 
 // ... or, for a batch of at most 32 tasks, as the last task whose first tile
@@ -70,10 +121,15 @@ struct ScanLookup {
     const TaskArgs *tasks;
     const unsigned long long *tile_first;
     int ntasks;
+    unsigned long long total;
     __device__ __forceinline__ int task_of(unsigned long long tg, int lane) const
     {
         const unsigned m = __ballot_sync(0xFFFFFFFFu, lane < ntasks && tile_first[lane] <= tg);
         return 31 - __clz((int)m);
+    }
+    __device__ __forceinline__ unsigned long long tiles_of(int t) const
+    {
+        return (t + 1 < ntasks ? tile_first[t + 1] : total) - tile_first[t];
     }
 };
 
@@ -91,7 +147,7 @@ struct ScanLookup {
 // where the tiles are too few for their sizes to need balancing.
 template <int K, int R, bool PF, bool STATIC, class Lookup, bool SMALL = false>
 __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long *counter, unsigned long long total_tiles,
-                                           int tile_blocks, const uint32_t *s_crc)
+                                           int tile_blocks, const uint32_t *s_crc, const TaskDone &td)
 {
     const int lane = threadIdx.x & 31;
     CrcLane L;
@@ -100,6 +156,7 @@ __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long 
     st.init();
     int cur = -1;
     ft_stats *cur_stats = nullptr;
+    unsigned long long cur_tiles = 0;   // tiles of task cur this warp voted
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     unsigned long long next = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (;;) {
@@ -115,11 +172,16 @@ __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long 
         const int t = lk.task_of(tg, lane);
         const TaskArgs a = lk.tasks[t];
         if (t != cur) {
-            if (cur >= 0) st.flush(cur_stats, lane);
+            if (cur >= 0) {
+                st.flush(cur_stats, lane);
+                if (td.flag_out) finish_task(td, cur_stats, cur_tiles, lk.tiles_of(cur), lane);
+            }
             st.init();
             cur = t;
             cur_stats = a.stats;
+            cur_tiles = 0;
         }
+        ++cur_tiles;
         const unsigned long long k = tg - lk.tile_first[t];
         const unsigned long long b0 = k * (unsigned long long)tile_blocks;
         const unsigned long long b1 = min(b0 + (unsigned long long)tile_blocks, a.nfull);
@@ -133,7 +195,10 @@ __device__ __forceinline__ void vote_tiles(const Lookup &lk, unsigned long long 
             st.merge(ts);
         }
     }
-    if (cur >= 0) st.flush(cur_stats, lane);
+    if (cur >= 0) {
+        st.flush(cur_stats, lane);
+        if (td.flag_out) finish_task(td, cur_stats, cur_tiles, lk.tiles_of(cur), lane);
+    }
 }
 
 template <int K, int R, int W, bool PF>
@@ -143,8 +208,9 @@ __global__ void __launch_bounds__(W * 32, 1) batched_kernel(const GroupDev g)
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
     load_crc_tables<W>(s_crc);
     __syncthreads();
-    vote_tiles<K, R, PF, false>(MapLookup{g.tasks, g.tile_task, g.tile_first}, g.counter, g.total_tiles,
-                                g.tile_blocks, s_crc);
+    vote_tiles<K, R, PF, false>(MapLookup{g.tasks, g.tile_task, g.tile_first, g.t1, g.total_tiles}, g.counter,
+                                g.total_tiles, g.tile_blocks, s_crc,
+                                TaskDone{g.tiles_done, g.stats_base, g.stats_out, g.flag_out, g.seq, false});
     if (g.done_ctas)
         copy_out_if_last(CopyOut{g.done_ctas, nullptr, g.tasks + g.t0, g.t1 - g.t0, false, g.stats_base, g.stats_out});
 }
@@ -158,7 +224,7 @@ __global__ void __launch_bounds__(W * 32, 1) batched_small_kernel(const __grid_c
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    const ScanLookup lk{g.tasks, g.tile_first, g.ntasks};
+    const ScanLookup lk{g.tasks, g.tile_first, g.ntasks, g.total_tiles};
     {
         // ask L2 for the first block of the warp's first tile while the CRC
         // tables are copied
@@ -175,8 +241,13 @@ __global__ void __launch_bounds__(W * 32, 1) batched_small_kernel(const __grid_c
     __syncthreads();
     // the 8-warp instance serves groups of at most a few tiles per warp: the
     // SMALL block form (see vote_full_block)
-    vote_tiles<K, R, false, true, ScanLookup, W == 8>(lk, g.counter, g.total_tiles, g.tile_blocks, s_crc);
-    copy_out_if_last(CopyOut{g.done_ctas, g.counter, g.tasks, g.ntasks, true, g.stats_base, g.stats_out});
+    vote_tiles<K, R, false, true, ScanLookup, W == 8>(
+        lk, g.counter, g.total_tiles, g.tile_blocks, s_crc,
+        TaskDone{g.tiles_done, g.stats_base, g.stats_out, g.flag_out, g.seq, true});
+    // with per-task completion the tasks' last warps have handed off and reset
+    // the statistics already; the last CTA still resets the counters
+    copy_out_if_last(CopyOut{g.done_ctas, g.counter, g.tasks, g.flag_out ? 0 : g.ntasks, true, g.stats_base,
+                             g.stats_out});
 }
 
 template <int K, int R, int W, bool PF, bool SMALL>

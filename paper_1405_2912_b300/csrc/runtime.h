@@ -38,7 +38,10 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
 // the slot is copied to a.stats at the end.  FT_EAGAIN, with nothing
 // launched, for an empty task or when every slot is taken.  Not for a stream
 // that is being captured.
-int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg);
+// With flag set, the kernel writes seq to *flag (host-mapped) after the
+// statistics have reached a.stats.
+int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, unsigned long long *flag = nullptr,
+                   unsigned long long seq = 0);
 
 // One (element kind, R) group of a batch, as the batched kernel sees it.
 // tasks[t] for t in [t0, t1) belong to the group; the group's work is split
@@ -56,6 +59,13 @@ struct GroupDev {
     unsigned long long *done_ctas;   // CTAs finished, zeroed before the launch; nullptr: no copy-out
     const ft_stats *stats_base;      // the batch's statistics array (device)
     ft_stats *stats_out;             // its host-mapped copy
+    // Completion of each task on its own (flag_out set): the warp whose tiles
+    // complete task t copies its statistics to stats_out[i] and then writes
+    // seq to flag_out[i] (host-mapped), i = tasks[t].stats - stats_base;
+    // tiles_done[i] counts the task's voted tiles and is zero at launch.
+    unsigned long long *tiles_done;
+    unsigned long long *flag_out;
+    unsigned long long seq;
     int32_t tile_blocks;
     int32_t kind;
     int32_t R;

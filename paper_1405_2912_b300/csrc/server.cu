@@ -72,8 +72,22 @@ struct Slot {
     uint8_t *small_area = nullptr;
     unsigned long long *small_cnt = nullptr;   // 2 per group: tile counter, done counter
     ft_stats *small_stats = nullptr;           // one per request
+    unsigned long long *small_tiles = nullptr; // per request of a small batch: its tiles voted so far
     bool small_dirty = true;                   // re-initialise before the next small batch
     bool last_small = false;                   // the batch in flight took the small path
+    // Completion request by request: the kernels write the batch's sequence
+    // number to flags[i] (pinned, host-mapped) once request i's statistics
+    // are in host_stats[i], so a request is done as soon as its own tiles are
+    // voted, not when its whole batch is.  The slot itself is free for the
+    // next batch only once the batch's event has completed.
+    unsigned long long *flags = nullptr;
+    unsigned long long *flags_dev = nullptr;
+    unsigned long long seq = 0;
+    bool per_req = false;                      // the batch in flight completes request by request
+    std::vector<char> req_done;
+    size_t ndone = 0;
+    double last_check = 0.0;                   // last event query while requests were outstanding
+    bool ended = false;                        // the event was seen complete
     // a batch's (kind, R) groups after the first run on these streams, forked
     // from and joined back into `stream` with events
     cudaStream_t aux[3] = {};
@@ -117,7 +131,9 @@ struct GroupStreams {
     }
 };
 
-constexpr size_t kSmallCntBytes = 2 * ftv::kSmallTasks * sizeof(unsigned long long);
+// the small-batch area: 2 counters per group, then a tile count per request
+// (all zero), then the requests' statistics
+constexpr size_t kSmallCntBytes = 3 * ftv::kSmallTasks * sizeof(unsigned long long);
 constexpr size_t kSmallAreaBytes = kSmallCntBytes + ftv::kSmallTasks * sizeof(ft_stats);
 
 ft_stats initial_stats()
@@ -150,6 +166,7 @@ struct ft_server {
     bool paused = false;
     std::vector<Slot> slots;
     std::thread worker;
+    unsigned long long batch_seq = 0;  // sequence number of the last batch launched (worker only)
     // counters reported by ft_server_info
     unsigned long long batches = 0, batched_requests = 0, completed = 0;
     int busy_now = 0, busy_max = 0;
@@ -161,28 +178,101 @@ struct ft_server {
 
 namespace {
 
-// Mark the requests of slot si done (lock held).
+// Request i of slot si is done with `status` (lock held).
+void complete_request(ft_server *s, Slot &sl, size_t i, double t, int status)
+{
+    sl.req_done[i] = 1;
+    sl.ndone += 1;
+    s->completed += 1;
+    auto it = s->reqs.find(sl.tickets[i]);
+    if (it == s->reqs.end()) return;
+    Request &r = it->second;
+    r.result = sl.host_stats[i];
+    r.status = status;
+    r.done = true;
+    r.done_us = t;
+    r.launch_us = sl.launched_at;
+    r.launched_us = sl.launch_done_at;
+}
+
+// The batch of slot si has left the device: its remaining requests are done
+// with the batch's status, and the slot takes the next batch (lock held).
 void complete_slot(ft_server *s, int si, double t)
 {
     Slot &sl = s->slots[si];
-    for (size_t i = 0; i < sl.tickets.size(); ++i) {
-        auto it = s->reqs.find(sl.tickets[i]);
-        if (it == s->reqs.end()) continue;
-        Request &r = it->second;
-        r.result = sl.host_stats[i];
-        r.status = sl.status;
-        r.done = true;
-        r.done_us = t;
-        r.launch_us = sl.launched_at;
-        r.launched_us = sl.launch_done_at;
-    }
+    for (size_t i = 0; i < sl.tickets.size(); ++i)
+        if (!sl.req_done[i]) complete_request(s, sl, i, t, sl.status);
     if (sl.last_small && sl.status != FT_OK) sl.small_dirty = true;
-    s->completed += sl.tickets.size();
     s->batch_span_us += t - sl.launched_at;
     sl.tickets.clear();
     sl.busy = false;
     s->busy_now -= 1;
     s->cv_done.notify_all();
+}
+
+// Requests of a batch with per-request completion whose flag is set
+// (lock held); returns how many.
+size_t reap_flags(ft_server *s, Slot &sl, double t)
+{
+    size_t k = 0;
+    for (size_t i = 0; i < sl.tickets.size(); ++i)
+        if (!sl.req_done[i] && __atomic_load_n(&sl.flags[i], __ATOMIC_ACQUIRE) == sl.seq) {
+            complete_request(s, sl, i, t, FT_OK);
+            ++k;
+        }
+    return k;
+}
+
+// While requests of a batch are outstanding its event is queried at most this
+// often (µs): a batch whose kernels ended without flagging a request (a CUDA
+// failure) completes through it.
+constexpr double kEventCheckUs = 100.0;
+
+// Completions of slot si (lock held).  Returns true when something changed.
+bool reap_slot(ft_server *s, int si)
+{
+    Slot &sl = s->slots[si];
+    const double t = now_us();
+    bool changed = false;
+    if (sl.per_req) {
+        if (reap_flags(s, sl, t)) {
+            changed = true;
+            s->cv_done.notify_all();
+        }
+        if (sl.ndone < sl.tickets.size() && !sl.ended) {
+            if (t - sl.last_check < kEventCheckUs) return changed;
+            sl.last_check = t;
+        }
+    }
+    const cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) return changed;
+    if (q != cudaSuccess) sl.status = ftv::cuda_fail(q);
+    if (sl.per_req && sl.status == FT_OK) {
+        // the kernels have ended: every flag they wrote is visible
+        reap_flags(s, sl, t);
+        // a request that the kernels left unflagged did not complete
+        if (sl.ndone < sl.tickets.size()) sl.status = FT_ECUDA;
+    }
+    complete_slot(s, si, t);
+    return true;
+}
+
+// Whether slot si has anything to reap (no lock: only the worker changes a
+// busy slot's fields).
+bool slot_progress(Slot &sl)
+{
+    if (sl.per_req) {
+        for (size_t i = 0; i < sl.tickets.size(); ++i)
+            if (!sl.req_done[i] && __atomic_load_n(&sl.flags[i], __ATOMIC_ACQUIRE) == sl.seq) return true;
+        if (sl.ndone < sl.tickets.size()) {
+            const double t = now_us();
+            if (t - sl.last_check < kEventCheckUs) return false;
+            sl.last_check = t;
+        }
+    }
+    if (cudaEventQuery(sl.done) == cudaErrorNotReady) return false;
+    sl.ended = true;   // reap_slot then completes the batch without waiting for its next check
+    return true;
 }
 
 int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
@@ -200,14 +290,20 @@ int grow_slot(Slot &sl, size_t layout_bytes, int nreq)
     }
     if (nreq > sl.cap) {
         if (sl.host_stats) cudaFreeHost(sl.host_stats);
+        if (sl.flags) cudaFreeHost(sl.flags);
         if (sl.dev_user) cudaFree(sl.dev_user);
         if (sl.host_user) cudaFreeHost(sl.host_user);
         sl.host_stats = nullptr;
+        sl.flags = nullptr;
         sl.dev_user = sl.host_user = nullptr;
         sl.cap = 0;
         if ((e = cudaMallocHost(&sl.host_stats, sizeof(ft_stats) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         if ((e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&sl.host_stats_dev), sl.host_stats, 0)) !=
             cudaSuccess)
+            return ftv::cuda_fail(e);
+        if ((e = cudaMallocHost(&sl.flags, sizeof(unsigned long long) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
+        std::memset(sl.flags, 0, sizeof(unsigned long long) * nreq);   // batch sequence numbers start at 1
+        if ((e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&sl.flags_dev), sl.flags, 0)) != cudaSuccess)
             return ftv::cuda_fail(e);
         if ((e = cudaMalloc(&sl.dev_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
         if ((e = cudaMallocHost(&sl.host_user, sizeof(ft_stats *) * nreq)) != cudaSuccess) return ftv::cuda_fail(e);
@@ -252,8 +348,8 @@ int group_warps(const ftv::TaskArgs &a, unsigned long long tiles, int max_ctas)
 }
 
 // A small batch: its (kind, R) groups are launched with their tasks in the
-// kernel parameters, so nothing is uploaded, and the statistics come back
-// through the group kernels' last CTAs.
+// kernel parameters, so nothing is uploaded, and each request's statistics
+// come back through the warp that votes its last tile, with its flag.
 int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int tile, int max_ctas)
 {
     const int n = (int)args.size();
@@ -295,11 +391,11 @@ int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int til
         g.done_ctas = sl.small_cnt + 2 * gi + 1;
         g.stats_base = sl.small_stats;
         g.stats_out = sl.host_stats_dev;
-        if (g.total_tiles == 0) {
-            // only empty requests: no kernel, and their statistics stay initial
-            for (int t = 0; t < g.ntasks; ++t) sl.host_stats[g.tasks[t].stats - sl.small_stats] = initial_stats();
-            continue;
-        }
+        g.tiles_done = sl.small_tiles;
+        g.flag_out = sl.flags_dev;
+        g.seq = sl.seq;
+        // only empty requests: no kernel (launch_slot has completed them)
+        if (g.total_tiles == 0) continue;
         cudaStream_t st = gs.get(launched++, &e);
         const int rc = e == cudaSuccess ? ftv::launch_small_group(g, st, max_ctas) : ftv::cuda_fail(e);
         if (rc != FT_OK) {
@@ -313,12 +409,22 @@ int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int til
 }
 
 // Launch the requests `tickets` as one batch on slot `si` (lock not held).
+// Without caller statistics pointers each request completes on its own (its
+// flag); with them, the statistics are scattered to the callers' buffers after
+// the group kernels and the batch completes as a whole (its event).
 int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any_user)
 {
     Slot &sl = s->slots[si];
     const int n = (int)args.size();
     for (int i = 0; i < n; ++i) args[i].stats = nullptr;   // set below, after growing
-    int rc = FT_OK;
+    int rc = grow_slot(sl, 0, n);
+    if (rc != FT_OK) return rc;
+    // empty requests have nothing to vote: done at launch, statistics initial
+    for (int i = 0; i < n; ++i)
+        if (args[i].n == 0) {
+            sl.host_stats[i] = initial_stats();
+            __atomic_store_n(&sl.flags[i], sl.seq, __ATOMIC_RELEASE);
+        }
     int tile = s->cfg.tile_blocks;
     if (s->auto_tile) {
         unsigned long long total = 0;
@@ -331,7 +437,6 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     const int max_ctas = batch_max_ctas(s, args[0]);
     sl.last_small = n <= ftv::kSmallTasks && !any_user;
     if (sl.last_small) {
-        if ((rc = grow_slot(sl, 0, n)) != FT_OK) return rc;
         if (n == 1 && args[0].n > 0) {
             // a lone request runs as a single vote (its statistics through one
             // of the voter's slots, copied straight into this slot's pinned
@@ -342,7 +447,7 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
             a.stats = sl.host_stats_dev;
             ftv::VoteLaunch vl{};
             vl.max_ctas = max_ctas;
-            rc = ftv::vote_task_slot(a, sl.stream, &vl);
+            rc = ftv::vote_task_slot(a, sl.stream, &vl, sl.flags_dev, sl.seq);
             if (rc != FT_EAGAIN) {
                 sl.last_small = false;
                 return rc;
@@ -354,8 +459,10 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     // the statistics of the batch follow the layout in the same buffer, so
     // that one upload carries the layout, its zeroed tile and done counters and the
     // initialised statistics, and no reset kernel is needed
+    // (and then each request's count of voted tiles, zero)
     const size_t o_stats = ftv::BatchLayout::align(sl.layout.device_bytes());
-    const size_t bytes = o_stats + sizeof(ft_stats) * n;
+    const size_t o_tiles = o_stats + sizeof(ft_stats) * n;
+    const size_t bytes = o_tiles + sizeof(unsigned long long) * n;
     rc = grow_slot(sl, bytes, n);
     if (rc != FT_OK) return rc;
     ft_stats *dev_stats = reinterpret_cast<ft_stats *>(sl.dev + o_stats);
@@ -366,17 +473,23 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     const ft_stats init = initial_stats();
     ft_stats *host_init = reinterpret_cast<ft_stats *>(sl.host + o_stats);
     for (int i = 0; i < n; ++i) host_init[i] = init;
-    // each group kernel's last CTA writes the group's statistics straight into
-    // the slot's pinned array, so no download follows the kernels; a group
-    // without tiles (only empty requests) launches nothing and is filled here
+    std::memset(sl.host + o_tiles, 0, sizeof(unsigned long long) * n);
+    // the statistics go straight into the slot's pinned array, request by
+    // request (without caller pointers) or by each group kernel's last CTA,
+    // so no download follows the kernels; a group without tiles (only empty
+    // requests) launches nothing
     for (size_t gi = 0; gi < sl.gd.size(); ++gi) {
         ftv::GroupDev &g = sl.gd[gi];
         g.warps = group_warps(sl.layout.tasks[g.t0], g.total_tiles, max_ctas);
-        g.done_ctas = sl.layout.counters_dev + sl.gd.size() + gi;
         g.stats_base = dev_stats;
         g.stats_out = sl.host_stats_dev;
-        if (g.total_tiles == 0)
-            for (int t = g.t0; t < g.t1; ++t) sl.host_stats[sl.layout.user_index[t]] = init;
+        if (any_user) {
+            g.done_ctas = sl.layout.counters_dev + sl.gd.size() + gi;
+        } else {
+            g.tiles_done = reinterpret_cast<unsigned long long *>(sl.dev + o_tiles);
+            g.flag_out = sl.flags_dev;
+            g.seq = sl.seq;
+        }
     }
     cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return ftv::cuda_fail(e);
@@ -438,18 +551,13 @@ void worker_main(ft_server *s)
     std::unique_lock<std::mutex> lk(s->mu);
     double idle_since = now_us();
     for (;;) {
-        // 1. completions
+        // 1. completions: requests whose flags are set, and batches whose
+        //    events have completed
         bool any_busy = false;
         for (size_t i = 0; i < s->slots.size(); ++i) {
-            Slot &sl = s->slots[i];
-            if (!sl.busy) continue;
-            const cudaError_t q = cudaEventQuery(sl.done);
-            if (q == cudaErrorNotReady) {
-                any_busy = true;
-                continue;
-            }
-            if (q != cudaSuccess) sl.status = ftv::cuda_fail(q);
-            complete_slot(s, (int)i, now_us());
+            if (!s->slots[i].busy) continue;
+            reap_slot(s, (int)i);
+            any_busy |= s->slots[i].busy;
         }
         if (s->stop && !any_busy) break;
         int free_slot = -1;
@@ -462,18 +570,16 @@ void worker_main(ft_server *s)
                 // wait for a change without holding the lock, so that clients
                 // calling ft_submit / ft_poll meanwhile never queue behind
                 // the worker: a new request, pause or stop (the state
-                // version), or a batch in flight completing
-                int nb = 0;
-                cudaEvent_t ev[8];
-                for (size_t i = 0; i < s->slots.size(); ++i)
-                    if (s->slots[i].busy) ev[nb++] = s->slots[i].done;
+                // version), a request's flag, or a batch's event completing
+                // (only this thread changes the slots)
                 const unsigned long long ver = s->version.load(std::memory_order_acquire);
                 const double t_end = now_us() + kPollSliceUs;
                 lk.unlock();
                 for (bool changed = false; !changed && now_us() < t_end;) {
                     changed = s->version.load(std::memory_order_acquire) != ver;
-                    for (int k = 0; k < nb && !changed; ++k) changed = cudaEventQuery(ev[k]) != cudaErrorNotReady;
-                    if (!changed && nb == 0) std::this_thread::yield();
+                    for (size_t k = 0; k < s->slots.size() && !changed; ++k)
+                        if (s->slots[k].busy) changed = slot_progress(s->slots[k]);
+                    if (!changed && !any_busy) std::this_thread::yield();
                 }
                 lk.lock();
             } else {
@@ -488,6 +594,7 @@ void worker_main(ft_server *s)
         sl.tickets.clear();
         bool any_user = false;
         unsigned long long batch_bytes = 0, first_bytes = 0;
+        std::vector<unsigned long long> req_bytes;
         // the size rule holds only while another slot is free for the requests
         // it leaves waiting; on the last free slot everything waiting is packed
         int free_slots = 0;
@@ -512,10 +619,27 @@ void worker_main(ft_server *s)
             s->queue_us += now_us() - it->second.submit_us;
             batch_bytes += it->second.bytes;
             args.push_back(it->second.args);
+            req_bytes.push_back(rb);
             sl.tickets.push_back(tk);
             any_user |= it->second.user_stats != nullptr;
         }
         if (args.empty()) continue;
+        if (args.size() > 1) {
+            // smallest first: the batch's tiles are voted in request order
+            // (within each element type / R group), so its small requests
+            // complete, each on its own, before its large ones
+            std::vector<int> ord(args.size());
+            for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+            std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return req_bytes[x] < req_bytes[y]; });
+            std::vector<ftv::TaskArgs> a2(args.size());
+            std::vector<unsigned long long> t2(args.size());
+            for (size_t i = 0; i < ord.size(); ++i) {
+                a2[i] = args[ord[i]];
+                t2[i] = sl.tickets[ord[i]];
+            }
+            args.swap(a2);
+            sl.tickets.swap(t2);
+        }
         sl.busy = true;
         s->batches += 1;
         s->batched_requests += args.size();
@@ -523,8 +647,14 @@ void worker_main(ft_server *s)
         s->busy_max = std::max(s->busy_max, s->busy_now);
         std::vector<ft_stats *> users(args.size());
         for (size_t i = 0; i < args.size(); ++i) users[i] = s->reqs[sl.tickets[i]].user_stats;
+        sl.seq = ++s->batch_seq;
+        sl.req_done.assign(args.size(), 0);
+        sl.ndone = 0;
+        sl.per_req = false;
+        sl.ended = false;
         lk.unlock();
         sl.launched_at = now_us();
+        sl.last_check = sl.launched_at;
         int rc = FT_OK;
         if (any_user) {
             rc = grow_slot(sl, 0, (int)args.size());
@@ -532,6 +662,7 @@ void worker_main(ft_server *s)
         }
         if (rc == FT_OK) rc = launch_slot(s, free_slot, args, any_user);
         sl.status = rc;
+        sl.per_req = rc == FT_OK && !any_user;
         cudaError_t e = cudaEventRecord(sl.done, sl.stream);
         sl.launch_done_at = now_us();
         const double launched = sl.launch_done_at - sl.launched_at;
@@ -558,6 +689,7 @@ void free_server(ft_server *s)
         if (sl.dev) cudaFree(sl.dev);
         if (sl.host) cudaFreeHost(sl.host);
         if (sl.host_stats) cudaFreeHost(sl.host_stats);
+        if (sl.flags) cudaFreeHost(sl.flags);
         if (sl.dev_user) cudaFree(sl.dev_user);
         if (sl.host_user) cudaFreeHost(sl.host_user);
         if (sl.small_area) cudaFree(sl.small_area);
@@ -623,6 +755,7 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
             break;
         }
         sl.small_cnt = reinterpret_cast<unsigned long long *>(sl.small_area);
+        sl.small_tiles = sl.small_cnt + 2 * ftv::kSmallTasks;
         sl.small_stats = reinterpret_cast<ft_stats *>(sl.small_area + kSmallCntBytes);
     }
     if (rc != FT_OK) {

@@ -183,6 +183,8 @@ struct SlotRef {
     StatsSlot *slot;               // nullptr: statistics go straight to a.stats
     unsigned int *busy;            // host-mapped free flag of the slot (0 = free)
     int wait_early;                // wait for the predecessor before reading the replicas
+    unsigned long long *flag;      // with a slot: set to seq (host-mapped) once a.stats holds the result
+    unsigned long long seq;
 };
 
 constexpr int kSlots = 1024;
@@ -273,6 +275,7 @@ __device__ __noinline__ void slot_finish(const SlotRef &sr, ft_stats *user)
         unsigned long long *w = reinterpret_cast<unsigned long long *>(&sr.slot->s) + threadIdx.x;
         reinterpret_cast<unsigned long long *>(user)[threadIdx.x] = __ldcg(w);
         *w = (threadIdx.x < FT_MAX_R || threadIdx.x == 2 * FT_MAX_R) ? 0ull : ~0ull;
+        if (sr.flag) __threadfence_system();   // the copy reaches the host before the flag
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -282,6 +285,7 @@ __device__ __noinline__ void slot_finish(const SlotRef &sr, ft_stats *user)
         // reads the flag sees them; only the GPU reads the slot
         __threadfence();
         *reinterpret_cast<volatile unsigned int *>(sr.busy) = 0u;
+        if (sr.flag) *reinterpret_cast<volatile unsigned long long *>(sr.flag) = sr.seq;
     }
 }
 
@@ -452,7 +456,8 @@ static int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg,
     }
 }
 
-int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
+int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, unsigned long long *flag,
+                   unsigned long long seq)
 {
     if (a.n == 0) return FT_EAGAIN;
     int dev = 0;
@@ -461,7 +466,7 @@ int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg)
     SlotPool *pool = slot_pool(dev);
     const int i = pool ? acquire_slot(*pool) : -1;
     if (i < 0) return FT_EAGAIN;
-    const int rc = launch_vote(a, s, cfg, SlotRef{pool->dev + i, pool->busy_dev + i, 1});
+    const int rc = launch_vote(a, s, cfg, SlotRef{pool->dev + i, pool->busy_dev + i, 1, flag, seq});
     if (rc != FT_OK) release_slot(*pool, i);
     return rc;
 }
@@ -486,7 +491,7 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)
         if (e != cudaSuccess) return cuda_fail(e);
         if ((rc = check_launch(1)) != FT_OK) return rc;
         if (desc->n == 0) return FT_OK;
-        return launch_vote(make_task_args(desc), s, cfg, SlotRef{nullptr, nullptr, 1});
+        return launch_vote(make_task_args(desc), s, cfg, SlotRef{nullptr, nullptr, 1, nullptr, 0});
     }
     if (desc->n > 0 && mode != 1) {
         // one launch: the statistics go through a slot, unless the stream is
@@ -499,7 +504,7 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)
             SlotPool *pool = slot_pool(dev);
             const int i = pool ? acquire_slot(*pool) : -1;
             if (i >= 0) {
-                rc = launch_vote(make_task_args(desc), s, cfg, SlotRef{pool->dev + i, pool->busy_dev + i, 1});
+                rc = launch_vote(make_task_args(desc), s, cfg, SlotRef{pool->dev + i, pool->busy_dev + i, 1, nullptr, 0});
                 if (rc != FT_OK) release_slot(*pool, i);   // the kernel did not start
                 return rc;
             }
@@ -509,7 +514,7 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)
     reset_stats_kernel<<<1, FT_MAX_R + 1, 0, s>>>(desc->stats);
     if ((rc = check_launch(1)) != FT_OK) return rc;
     if (desc->n == 0) return FT_OK;
-    return launch_vote(make_task_args(desc), s, cfg, SlotRef{nullptr, nullptr, 0});
+    return launch_vote(make_task_args(desc), s, cfg, SlotRef{nullptr, nullptr, 0, nullptr, 0});
 }
 
 // ---------------------------------------------------------------------------

@@ -3,12 +3,12 @@
 A load generator for the serving form: it submits each request at its
 scheduled arrival time (host monotonic clock of the library, ft_clock_us),
 retries requests that the budget refuses, collects results in arrival order,
-and reports latency = completion time (when the server's worker saw the batch complete) minus
-the scheduled arrival time, so that queueing behind the budget and in the
-server both count.  Each pass of its loop submits every request that has
-arrived with one ft_submit_many and retires the finished ones with one
-ft_poll_many, so the generator's own cost does not grow with the request
-rate.  It only calls the C ABI; all voting runs on the GPU.
+and reports latency = completion time (when the server's worker saw the
+request complete) minus the scheduled arrival time, so that queueing behind
+the budget and in the server both count.  Each pass of its loop submits every
+request that has arrived with one ft_submit_many, and retires the finished
+ones with one ft_poll_many every so often, so the generator's own cost does
+not grow with the request rate.  It only calls the C ABI; all voting runs on the GPU.
 """
 from __future__ import annotations
 
@@ -21,26 +21,29 @@ import numpy as np
 from . import ftvote as fv
 
 
-def replay(srv, descs, arrivals_s, payload_of, start_delay_us=2000.0):
+def replay(srv, descs, arrivals_s, payload_of, start_delay_us=2000.0, poll_every_us=50.0):
     """Submit descs[payload_of[i]] at arrivals_s[i] seconds after the start.
 
     Returns a dict with per-request latencies (us), the number of budget
     refusals, and the wall span from the first arrival to the last completion.
     Python's cyclic garbage collector is paused for the replay: one of its
     full collections stalls the submitting loop for milliseconds, which would
-    show as server latency.
+    show as server latency.  Finished requests are collected at most every
+    poll_every_us: a request's completion time is the server's, so collecting
+    it later changes no latency, and fewer polls leave the loop free to submit
+    on time and the server's lock to its worker.
     """
     was_enabled = gc.isenabled()
     gc.collect()
     gc.disable()
     try:
-        return _replay(srv, descs, arrivals_s, payload_of, start_delay_us)
+        return _replay(srv, descs, arrivals_s, payload_of, start_delay_us, poll_every_us)
     finally:
         if was_enabled:
             gc.enable()
 
 
-def _replay(srv, descs, arrivals_s, payload_of, start_delay_us):
+def _replay(srv, descs, arrivals_s, payload_of, start_delay_us, poll_every_us):
     n = len(arrivals_s)
     m = max(n, 1)
     # one descriptor pointer, ticket and result slot per request, laid out
@@ -55,16 +58,24 @@ def _replay(srv, descs, arrivals_s, payload_of, start_delay_us):
     submit_many, poll_many, clock = fv.ft_submit_many, fv.ft_poll_many, fv.ft_clock_us
     t0 = clock() + start_delay_us
     arr = t0 + np.asarray(arrivals_s, dtype=np.float64) * 1e6
+    arr_l = arr.tolist()                  # scalar reads of a list are cheaper than of an array
     i = head = 0
     refused = 0
+    last_poll = 0.0
     while head < n:
-        due = int(np.searchsorted(arr, clock(), side="right"))   # arrivals that have passed
+        now = clock()
+        due = i
+        while due < n and arr_l[due] <= now:   # arrivals that have passed
+            due += 1
+        blocked = False
         if due > i:
             fv.check(submit_many(srv, a_d + 8 * i, due - i, a_t + 8 * i, pacc), "ft_submit_many")
-            if acc.value < due - i:
-                refused += 1              # the budget is full: retry on the next pass
+            blocked = acc.value < due - i
+            if blocked:
+                refused += 1              # the budget is full: collect, then retry on the next pass
             i += acc.value
-        if head < i:
+        if head < i and (blocked or i == n or now - last_poll >= poll_every_us):
+            last_poll = now
             rc = poll_many(srv, a_t + 8 * head, i - head, 0, a_r + rsz * head, pnd)
             if rc != fv.FT_ETIMEDOUT:
                 fv.check(rc, "ft_poll_many")

@@ -330,8 +330,9 @@ def test_bulk_submit_and_poll():
 @pytest.mark.parametrize("user_stats", [False, True])
 def test_empty_requests_and_groups_in_a_batch(user_stats):
     """One batch holding empty requests: inside a (kind, R) group that has
-    tiles (the group kernel's last CTA copies their statistics out) and as the
-    whole of a group (no kernel runs for it; the server fills them).  Every
+    tiles and as the whole of a group (no kernel runs for it); the server
+    completes them at launch, or with the group kernel's copy-out where the
+    caller gave statistics pointers.  Every
     empty request reads (0, -1) for all replicas; the others match the
     oracle.  Without caller statistics pointers the batch travels in the
     kernel parameters; one caller pointer sends it through the upload path
@@ -464,3 +465,57 @@ def test_size_rule_keeps_small_requests_out_of_a_large_ones_batch():
         fv.ft_server_destroy(srv)
     for p, t in zip(probs, tasks):
         assert_same(t.result(), oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol), p.R)
+
+
+@pytest.mark.parametrize("nsmall", [5, 20])
+def test_requests_complete_on_their_own_inside_a_batch(nsmall):
+    """Small requests packed into one batch with a large one complete as soon
+    as their own tiles are voted, before the large one: the batch runs its
+    requests smallest first, and the warp that votes a request's last tile
+    flags it to the host.  Five small requests travel in the kernel
+    parameters, twenty through the upload path; some of them in a second
+    (kind, R) group.  Every result equals the oracle's."""
+    from paper_1405_2912_b300 import ftvote as fv
+    big = synth.task_problem(synth.TaskSpec(1 << 26, "f32", 3, True, 61), config_id=5)
+    small = [synth.task_problem(synth.TaskSpec(4096 * (1 + i % 3) + 7 * i, ["f32", "f64"][i % 2], [3, 5][i % 2],
+                                               i % 3 == 0, 70 + i), config_id=5)
+             for i in range(nsmall)]
+    probs = [big] + small                 # the large one is the oldest
+    tasks = [DevTask(p) for p in probs]
+    # two streams: the batch's kernels leave SMs free, on which the second
+    # group's kernel runs beside the first's
+    srv = _server(budget=1 << 36, max_slots=64, streams=2, tile=0, size_ratio=-1)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tks = []
+        for t in tasks:
+            d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+            d.stats = None
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)) == fv.FT_OK
+            tks.append(tk.value)
+        fv.ft_server_pause(srv, 0)
+        res = []
+        for tk in tks:
+            r = fv.ft_result()
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+            assert r.status == fv.FT_OK
+            res.append(r)
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        assert info.batches == 1
+        assert len({r.launch_us for r in res}) == 1
+        # 1 GiB of replicas takes well over 100 us; the small ones finish first
+        assert max(r.done_us for r in res[1:]) < res[0].done_us
+    finally:
+        fv.ft_server_destroy(srv)
+    for p, t, r in zip(probs, tasks, res):
+        ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        got = t.result()
+        assert got["out"].tobytes() == ref["out"].tobytes()
+        assert np.array_equal(got["block_crc"], ref["block_crc"])
+        sd = _stats_dict(r.stats, p.R)
+        assert [int(x) for x in sd["mismatch"]] == [int(x) for x in ref["mismatch"]]
+        assert [int(x) for x in sd["first_mismatch"]] == [int(x) for x in ref["first_mismatch"]]
+        assert sd["no_majority"] == int(ref["no_majority"])
+        assert sd["first_no_majority"] == int(ref["first_no_majority"])
