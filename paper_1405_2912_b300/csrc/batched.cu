@@ -217,6 +217,23 @@ void BatchLayout::pack(uint8_t *host, uint8_t *dev, std::vector<GroupDev> &gd)
     mixed.tile_blocks = tile_blocks_;
 }
 
+int preload_group_kernels()
+{
+    for (int kind : {K_F32, K_F64, K_B1, K_B4, K_B8})
+        for (int R = 2; R <= FT_MAX_R; ++R)
+            for (int w : {8, 16})
+                for (bool small : {false, true}) {
+                    const void *fn = group_kernel(kind, R, w, false, small);
+                    if (!fn) return FT_EINVAL;
+                    int sms = 0, per_sm = 0;
+                    const int rc = occupancy(fn, w * 32, kSmemBytes, &sms, &per_sm);
+                    if (rc != FT_OK) return rc;
+                }
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(stats_scatter_kernel));
+    return e == cudaSuccess ? FT_OK : cuda_fail(e);
+}
+
 int launch_groups(const std::vector<GroupDev> &gd, int ctas_per_sm, cudaStream_t s, int max_ctas)
 {
     int rc = FT_OK;

@@ -43,6 +43,15 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
 int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, unsigned long long *flag = nullptr,
                    unsigned long long seq = 0);
 
+// With lazy module loading (the CUDA default) a kernel is loaded at its first
+// launch, 0.1-0.4 ms of host time on B300.  These load, and size for the CRC
+// tables' shared memory, every single-task voter shape the library picks by
+// itself (and create the device's statistics slots), and every batched and
+// small-batch kernel of the shapes the server launches, so that a long-lived
+// caller (the server) pays that once at creation instead of inside a request.
+int preload_vote_kernels();
+int preload_group_kernels();
+
 // One (element kind, R) group of a batch, as the batched kernel sees it.
 // tasks[t] for t in [t0, t1) belong to the group; the group's work is split
 // into total_tiles tiles of tile_blocks 4 KiB blocks; tile_task[g] is the task

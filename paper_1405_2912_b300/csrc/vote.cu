@@ -456,6 +456,50 @@ static int launch_vote(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg,
     }
 }
 
+// Loads (and sets up for the library's shared memory) every shape of K1 that
+// launch_vote_kr picks without a tuning override for (K, R).
+template <int K, int R>
+static int preload_vote_kr()
+{
+    using P = VotePolicy<K, R>;
+    constexpr int JB = kSubBatch<K, R>;
+    int sms = 0, per_sm = 0, rc;
+    if ((rc = occupancy(reinterpret_cast<const void *>(vote_kernel<K, R, kTinyWarps, false, JB, true>),
+                        kTinyWarps * 32, kSmemBytes, &sms, &per_sm)) != FT_OK ||
+        (rc = occupancy(reinterpret_cast<const void *>(vote_kernel<K, R, 16, false, JB, true>), 16 * 32, kSmemBytes,
+                        &sms, &per_sm)) != FT_OK ||
+        (rc = occupancy(reinterpret_cast<const void *>(vote_kernel<K, R, 16, false, JB, false>), 16 * 32,
+                        kSmemBytes, &sms, &per_sm)) != FT_OK)
+        return rc;
+    return occupancy(reinterpret_cast<const void *>(vote_kernel<K, R, P::kWarps, P::kPrefetch, JB, false>),
+                     P::kWarps * 32, kSmemBytes, &sms, &per_sm);
+}
+
+template <int K>
+static int preload_vote_k()
+{
+    int rc;
+    if ((rc = preload_vote_kr<K, 2>()) != FT_OK || (rc = preload_vote_kr<K, 3>()) != FT_OK ||
+        (rc = preload_vote_kr<K, 4>()) != FT_OK || (rc = preload_vote_kr<K, 5>()) != FT_OK ||
+        (rc = preload_vote_kr<K, 6>()) != FT_OK || (rc = preload_vote_kr<K, 7>()) != FT_OK)
+        return rc;
+    return preload_vote_kr<K, 8>();
+}
+
+int preload_vote_kernels()
+{
+    int rc;
+    if ((rc = preload_vote_k<K_F32>()) != FT_OK || (rc = preload_vote_k<K_F64>()) != FT_OK ||
+        (rc = preload_vote_k<K_B1>()) != FT_OK || (rc = preload_vote_k<K_B4>()) != FT_OK ||
+        (rc = preload_vote_k<K_B8>()) != FT_OK)
+        return rc;
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    slot_pool(dev);   // the statistics slots too (a device without them votes through the reset kernel)
+    return FT_OK;
+}
+
 int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, unsigned long long *flag,
                    unsigned long long seq)
 {
