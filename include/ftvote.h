@@ -271,7 +271,9 @@ typedef struct ft_server ft_server;   /* library-owned */
 typedef struct ft_server_config {
     uint64_t mem_budget_bytes;  /* admission budget: sum over admitted, not yet
                                    collected requests of (R+1) * n * sizeof(dtype) */
-    int32_t  max_slots;         /* most requests packed into one batch (1..65536) */
+    int32_t  max_slots;         /* most requests packed into one batch (1..65536); the
+                                   requests waiting are spread evenly over the free streams,
+                                   so a batch packs several only when they outnumber them */
     int32_t  streams;           /* batches in flight at once (1..8)               */
     int32_t  tile_blocks;       /* batched-kernel tile, 1..64; 0 = automatic per batch:
                                    8, halved while the batch would make fewer tiles
@@ -313,9 +315,15 @@ typedef struct ft_result {
  * with up to three auxiliary streams, on which a batch's further element-type
  * / R groups run in parallel).  With two or more streams no batch's kernels
  * occupy more than all but cfg->reserved_sms SMs, so that a batch is not held
- * behind all of a large one.  The thread polls for new requests and finished
- * batches without holding the server's lock, and keeps polling for
- * cfg->idle_spin_us after its last batch before it sleeps.
+ * behind all of a large one.  A batch votes its requests smallest first, and
+ * a request without a caller statistics pointer completes as soon as its own
+ * tiles are voted: the kernel writes its statistics and a completion flag to
+ * host-mapped memory (requests with caller pointers complete with their whole
+ * batch).  The thread polls for new requests and completions without holding
+ * the server's lock, and keeps polling for cfg->idle_spin_us after its last
+ * batch before it sleeps.  Creation loads every kernel the server can launch
+ * (a few tens of milliseconds the first time in a process), so that no
+ * request pays CUDA's lazy loading of a kernel at its first launch.
  * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
 int ft_server_create(ft_server **srv, const ft_server_config *cfg);
 
