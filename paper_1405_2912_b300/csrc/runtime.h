@@ -42,6 +42,16 @@ int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg);
 // statistics have reached a.stats.
 int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, unsigned long long *flag = nullptr,
                    unsigned long long seq = 0);
+// The same in two steps, for a caller that launches several votes and must
+// know before the first that each gets a statistics slot: reserve_vote_slot
+// takes a free slot of the current device (-1 when all are taken),
+// vote_task_reserved launches a non-empty task on it (the kernel frees the
+// slot at its end; a failed launch frees it at once), and release_vote_slot
+// frees a reserved slot that no vote was launched on.
+int reserve_vote_slot();
+void release_vote_slot(int slot);
+int vote_task_reserved(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, int slot, unsigned long long *flag,
+                       unsigned long long seq);
 
 // With lazy module loading (the CUDA default) a kernel is loaded at its first
 // launch, 0.1-0.4 ms of host time on B300.  These load, and size for the CRC

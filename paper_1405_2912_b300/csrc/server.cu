@@ -349,11 +349,16 @@ int group_warps(const ftv::TaskArgs &a, unsigned long long tiles, int max_ctas)
 
 // A small batch: its (kind, R) groups are launched with their tasks in the
 // kernel parameters, so nothing is uploaded, and each request's statistics
-// come back through the warp that votes its last tile, with its flag.
-int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int tile, int max_ctas)
+// come back through the warp that votes its last tile, with its flag.  The
+// requests with skip[i] set are left out (they vote on their own).  Group g
+// runs on gs's stream g; *launched returns how many streams were used.  The
+// caller joins gs.
+int launch_small_batch(Slot &sl, GroupStreams &gs, const std::vector<ftv::TaskArgs> &args, const bool *skip,
+                       int tile, int max_ctas, int *launched_out)
 {
-    const int n = (int)args.size();
+    const int n_all = (int)args.size();
     cudaError_t e;
+    *launched_out = 0;
     if (sl.small_dirty) {
         // first use, or a failed batch may have left counters or statistics set
         uint8_t init[kSmallAreaBytes];
@@ -367,12 +372,13 @@ int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int til
         sl.small_dirty = false;
     }
     int order[ftv::kSmallTasks];
-    for (int i = 0; i < n; ++i) order[i] = i;
+    int n = 0;
+    for (int i = 0; i < n_all; ++i)
+        if (!skip[i]) order[n++] = i;
     std::stable_sort(order, order + n, [&](int x, int y) {
         return std::make_pair(args[x].kind, args[x].R) < std::make_pair(args[y].kind, args[y].R);
     });
     ftv::SmallGroup g;
-    GroupStreams gs{sl};
     int gi = 0, launched = 0;
     for (int i = 0; i < n; ++gi) {
         std::memset(&g, 0, sizeof g);
@@ -397,15 +403,27 @@ int launch_small_batch(Slot &sl, const std::vector<ftv::TaskArgs> &args, int til
         // only empty requests: no kernel (launch_slot has completed them)
         if (g.total_tiles == 0) continue;
         cudaStream_t st = gs.get(launched++, &e);
+        *launched_out = launched;
         const int rc = e == cudaSuccess ? ftv::launch_small_group(g, st, max_ctas) : ftv::cuda_fail(e);
         if (rc != FT_OK) {
             sl.small_dirty = true;
-            gs.join();
             return rc;
         }
     }
-    if ((e = gs.join()) != cudaSuccess) return ftv::cuda_fail(e);
     return FT_OK;
+}
+
+// Request bytes from which a request of a small batch votes on its own, as a
+// single vote through the single-task voter, instead of in the batch's group
+// kernel: (R+1) x its bytes, 64 MiB (10 us of HBM time).  It then gets the
+// single-task shapes (for f32 R = 3 the prefetching 12-warp one), runs on a
+// stream of its own beside the batch's small requests, and does not wait for
+// them.
+constexpr unsigned long long kOwnVoteBytes = 64ull << 20;
+
+unsigned long long task_bytes(const ftv::TaskArgs &a)
+{
+    return (unsigned long long)(a.R + 1) * (a.nfull * FT_BLOCK_BYTES + a.tail_bytes);
 }
 
 // Launch the requests `tickets` as one batch on slot `si` (lock not held).
@@ -437,23 +455,52 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
     const int max_ctas = batch_max_ctas(s, args[0]);
     sl.last_small = n <= ftv::kSmallTasks && !any_user;
     if (sl.last_small) {
-        if (n == 1 && args[0].n > 0) {
-            // a lone request runs as a single vote (its statistics through one
-            // of the voter's slots, copied straight into this slot's pinned
-            // array), which takes the single-task shapes: 3.1 us less kernel
-            // time than the batched kernel at 16 KiB per replica, and the
-            // prefetching 12-warp shape for large f32 R = 3 votes
-            ftv::TaskArgs a = args[0];
-            a.stats = sl.host_stats_dev;
+        // A lone request, and each large one, votes on its own through the
+        // single-task voter (its statistics through one of the voter's slots,
+        // copied straight into this slot's pinned array, then its flag): the
+        // single-task shapes take 3.1 us less kernel time than the batched
+        // kernel at 16 KiB per replica, and for large f32 R = 3 votes the
+        // prefetching 12-warp shape.  If the voter's slots run out, every
+        // request goes through the small-batch kernels.
+        bool own[ftv::kSmallTasks] = {};
+        int vslot[ftv::kSmallTasks];
+        for (int i = 0; i < n; ++i) {
+            if (args[i].n == 0 || (n > 1 && task_bytes(args[i]) < kOwnVoteBytes)) continue;
+            if ((vslot[i] = ftv::reserve_vote_slot()) < 0) {
+                for (int k = 0; k < i; ++k)
+                    if (own[k]) ftv::release_vote_slot(vslot[k]);
+                std::fill(own, own + n, false);
+                break;
+            }
+            own[i] = true;
+        }
+        bool any_small = false;
+        for (int i = 0; i < n; ++i) any_small |= !own[i] && args[i].n > 0;
+        GroupStreams gs{sl};
+        int used = 0;
+        if (any_small) rc = launch_small_batch(sl, gs, args, own, tile, max_ctas, &used);
+        else sl.last_small = false;   // the small-batch area is not used
+        // the requests voting on their own one after another (smallest first),
+        // on the stream after the small requests' groups
+        cudaStream_t st = nullptr;
+        for (int i = 0; i < n; ++i) {
+            if (!own[i]) continue;
+            cudaError_t e = cudaSuccess;
+            if (rc == FT_OK && !st) st = gs.get(used, &e);
+            if (rc == FT_OK && e != cudaSuccess) rc = ftv::cuda_fail(e);
+            if (rc != FT_OK) {
+                ftv::release_vote_slot(vslot[i]);
+                continue;
+            }
+            ftv::TaskArgs a = args[i];
+            a.stats = sl.host_stats_dev + i;
             ftv::VoteLaunch vl{};
             vl.max_ctas = max_ctas;
-            rc = ftv::vote_task_slot(a, sl.stream, &vl, sl.flags_dev, sl.seq);
-            if (rc != FT_EAGAIN) {
-                sl.last_small = false;
-                return rc;
-            }
+            rc = ftv::vote_task_reserved(a, st, &vl, vslot[i], sl.flags_dev + i, sl.seq);
         }
-        return launch_small_batch(sl, args, tile, max_ctas);
+        const cudaError_t je = gs.join();
+        if (rc == FT_OK && je != cudaSuccess) rc = ftv::cuda_fail(je);
+        return rc;
     }
     sl.layout.build(args, tile);
     // the statistics of the batch follow the layout in the same buffer, so

@@ -500,19 +500,42 @@ int preload_vote_kernels()
     return FT_OK;
 }
 
+int reserve_vote_slot()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    SlotPool *pool = slot_pool(dev);
+    return pool ? acquire_slot(*pool) : -1;
+}
+
+void release_vote_slot(int slot)
+{
+    int dev = 0;
+    if (slot < 0 || cudaGetDevice(&dev) != cudaSuccess) return;
+    SlotPool *pool = slot_pool(dev);
+    if (pool) release_slot(*pool, slot);
+}
+
+int vote_task_reserved(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, int slot, unsigned long long *flag,
+                       unsigned long long seq)
+{
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    SlotPool *pool = slot_pool(dev);
+    if (!pool || slot < 0 || slot >= kSlots || a.n == 0) return FT_EINVAL;
+    const int rc = launch_vote(a, s, cfg, SlotRef{pool->dev + slot, pool->busy_dev + slot, 1, flag, seq});
+    if (rc != FT_OK) release_slot(*pool, slot);   // the kernel did not start
+    return rc;
+}
+
 int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, unsigned long long *flag,
                    unsigned long long seq)
 {
     if (a.n == 0) return FT_EAGAIN;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e);
-    SlotPool *pool = slot_pool(dev);
-    const int i = pool ? acquire_slot(*pool) : -1;
+    const int i = reserve_vote_slot();
     if (i < 0) return FT_EAGAIN;
-    const int rc = launch_vote(a, s, cfg, SlotRef{pool->dev + i, pool->busy_dev + i, 1, flag, seq});
-    if (rc != FT_OK) release_slot(*pool, i);
-    return rc;
+    return vote_task_reserved(a, s, cfg, i, flag, seq);
 }
 
 int vote_desc(const ft_vote_desc *desc, cudaStream_t s, const VoteLaunch *cfg)

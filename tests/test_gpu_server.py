@@ -525,3 +525,57 @@ def test_requests_complete_on_their_own_inside_a_batch(nsmall):
         assert [int(x) for x in sd["first_mismatch"]] == [int(x) for x in ref["first_mismatch"]]
         assert sd["no_majority"] == int(ref["no_majority"])
         assert sd["first_no_majority"] == int(ref["first_no_majority"])
+
+
+def test_large_requests_of_a_small_batch_vote_on_their_own():
+    """In a batch of at most 16 requests, each request of 64 MiB or more of
+    replicas and output votes on its own through the single-task voter, on a
+    stream beside the batch's small-batch kernels; the small requests share
+    one kernel per (kind, R) group.  Two large requests of different kinds,
+    three small ones in two groups and an empty one: four launches, and every
+    result equals the oracle's, statistics included."""
+    from paper_1405_2912_b300 import ftvote as fv
+    specs = [synth.TaskSpec(5000, "f32", 3, True, 81), synth.TaskSpec(0, "f32", 3, False, 82),
+             synth.TaskSpec(1 << 23, "f32", 3, True, 83), synth.TaskSpec(7000, "f64", 5, True, 84),
+             synth.TaskSpec(3 << 20, "f64", 5, True, 85), synth.TaskSpec(9000, "f32", 3, False, 86)]
+    probs = [synth.task_problem(sp, config_id=5, ulp_frac=0.05, flip_rate=1e-3) for sp in specs]
+    big = [(p.R + 1) * p.n * p.itemsize >= 64 << 20 for p in probs]
+    assert big == [False, False, True, False, True, False]
+    tasks = [DevTask(p) for p in probs]
+    srv = _server(budget=1 << 36, max_slots=16, streams=1, tile=0, size_ratio=-1)
+    try:
+        fv.ft_server_pause(srv, 1)
+        tks = []
+        for t in tasks:
+            d = fv.ft_vote_desc.from_buffer_copy(t.desc)
+            d.stats = None
+            tk = ctypes.c_uint64()
+            assert fv.ft_submit(srv, ctypes.byref(d), ctypes.byref(tk)) == fv.FT_OK
+            tks.append(tk.value)
+        l0 = fv.ft_launch_count()
+        fv.ft_server_pause(srv, 0)
+        res = []
+        for tk in tks:
+            r = fv.ft_result()
+            assert fv.ft_poll(srv, tk, 30_000_000, ctypes.byref(r)) == fv.FT_OK
+            assert r.status == fv.FT_OK
+            res.append(r)
+        launches = fv.ft_launch_count() - l0
+        info = fv.ft_server_stats()
+        fv.ft_server_info(srv, ctypes.byref(info))
+        assert info.batches == 1
+    finally:
+        fv.ft_server_destroy(srv)
+    # f32 R=3 and f64 R=5 small-batch kernels, and the two single votes
+    assert launches == 4
+    for p, t, r in zip(probs, tasks, res):
+        ref = oracle.vote(p.replicas, p.dtype, p.abs_tol, p.rel_tol)
+        sd = _stats_dict(r.stats, p.R)
+        assert [int(x) for x in sd["mismatch"]] == [int(x) for x in ref["mismatch"]]
+        assert [int(x) for x in sd["first_mismatch"]] == [int(x) for x in ref["first_mismatch"]]
+        assert sd["no_majority"] == int(ref["no_majority"])
+        assert sd["first_no_majority"] == int(ref["first_no_majority"])
+        if p.n:
+            got = t.result()
+            assert got["out"].tobytes() == ref["out"].tobytes()
+            assert np.array_equal(got["block_crc"], ref["block_crc"])
