@@ -315,8 +315,11 @@ typedef struct ft_result {
  * with up to three auxiliary streams, on which a batch's further element-type
  * / R groups run in parallel).  With two or more streams no batch's kernels
  * occupy more than all but cfg->reserved_sms SMs, so that a batch is not held
- * behind all of a large one.  A batch votes its requests smallest first, and
- * a request without a caller statistics pointer completes as soon as its own
+ * behind all of a large one.  A batch votes its requests smallest first; in
+ * a batch of at most 16 requests without caller statistics pointers, a lone
+ * request and each one of 64 MiB or more ((R+1) * n * sizeof(dtype)) runs as
+ * a single vote (the ft_vote kernels) beside the others' batched kernels.  A
+ * request without a caller statistics pointer completes as soon as its own
  * tiles are voted: the kernel writes its statistics and a completion flag to
  * host-mapped memory (requests with caller pointers complete with their whole
  * batch).  The thread polls for new requests and completions without holding
