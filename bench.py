@@ -948,7 +948,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the request stream (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-pool", type=int, default=64)
-    ap.add_argument("--serve-reps", type=int, default=3, help="replays of each serving arm (the median p99 is reported)")
+    ap.add_argument("--serve-reps", type=int, default=5, help="replays of each serving arm (the median p99 is reported)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.warmup < 3 and args.impl == "ours":
