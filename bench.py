@@ -468,7 +468,9 @@ def run_ours(args, problem, ws, rank, local):
 
 
 def batched_summary(b):
-    """The batched figures that the end of the JSON line carries."""
+    """The batched figures that the end of the JSON line carries (the tuned
+    launch shapes are in batched_detail: the batched and serving summaries
+    together stay within the last 1500 characters of the line)."""
     if not b:
         return None
     out = {"tasks": b["tasks"], "tasks_per_s": b["tasks_per_s"], "gb_per_s": b["gb_per_s"],
@@ -476,7 +478,7 @@ def batched_summary(b):
            "speedup_vs_per_task": b["speedup_vs_per_task"],
            "noalloc_tasks_per_s": b["noalloc"]["tasks_per_s"] if b.get("noalloc") else None,
            "one_kernel_tasks_per_s": b["one_kernel_for_the_batch"]["tasks_per_s"],
-           "launches_per_batch": b["launches_per_batch"], "tune": b["tune"]}
+           "launches_per_batch": b["launches_per_batch"]}
     return out
 
 
