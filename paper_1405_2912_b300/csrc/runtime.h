@@ -45,8 +45,9 @@ int vote_task_slot(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, uns
 // The same in two steps, for a caller that launches several votes and must
 // know before the first that each gets a statistics slot: reserve_vote_slot
 // takes a free slot of the current device (-1 when all are taken),
-// vote_task_reserved launches a non-empty task on it (the kernel frees the
-// slot at its end; a failed launch frees it at once), and release_vote_slot
+// vote_task_reserved launches a task on it, which must not be empty (the
+// kernel frees the slot at its end; a failed launch frees it at once), and
+// release_vote_slot
 // frees a reserved slot that no vote was launched on.
 int reserve_vote_slot();
 void release_vote_slot(int slot);
