@@ -64,7 +64,8 @@ FALLBACK_HBM_GBS = 6400.0
 L2_BYTES = 126 << 20
 
 
-KERNEL_SOURCES = ("paper_1405_2912_b300/csrc/common.cuh", "paper_1405_2912_b300/csrc/vote.cu")
+KERNEL_SOURCES = ("paper_1405_2912_b300/csrc/common.cuh", "paper_1405_2912_b300/csrc/vote_kernel.cuh",
+                  "paper_1405_2912_b300/csrc/vote.cu")
 TRAFFIC_FILES = {"f32x3-256M": "profiles/vote_f32_r3_256M_dram.txt",
                  "f64x5-64M": "profiles/vote_f64_r5_64M_dram.txt",
                  "i32x5-64M": "profiles/vote_i32_r5_64M_dram.txt"}

@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "runtime.h"
+#include "vote_kernel.cuh"
 
 namespace ftv {
 
@@ -173,20 +174,6 @@ __global__ void reset_stats_chained_kernel(ft_stats *s)
 // on.  When every slot is taken, and in a stream capture (a graph would bake
 // one slot into every replay), the vote falls back to the reset kernel.
 // ---------------------------------------------------------------------------
-struct StatsSlot {
-    ft_stats s;                    // same layout as the caller's
-    unsigned long long done;       // CTAs finished
-    unsigned long long pad_[5];    // one slot per 192 bytes
-};
-
-struct SlotRef {
-    StatsSlot *slot;               // nullptr: statistics go straight to a.stats
-    unsigned int *busy;            // host-mapped free flag of the slot (0 = free)
-    int wait_early;                // wait for the predecessor before reading the replicas
-    unsigned long long *flag;      // with a slot: set to seq (host-mapped) once a.stats holds the result
-    unsigned long long seq;
-};
-
 constexpr int kSlots = 1024;
 constexpr int kMaxDevices = 64;
 
@@ -255,103 +242,22 @@ static int acquire_slot(SlotPool &p)
 
 static void release_slot(SlotPool &p, int i) { __atomic_store_n(&p.busy[i], 0u, __ATOMIC_RELEASE); }
 
-// End of a slot vote, after every warp of the CTA has added its statistics to
-// the slot: the last CTA to arrive copies the slot to the caller's ft_stats
-// (entries beyond R are still at their initial values), resets it and marks
-// it free.
-__device__ __noinline__ void slot_finish(const SlotRef &sr, ft_stats *user)
-{
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&sr.slot->done, 1ull) == (unsigned long long)gridDim.x - 1ull;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    constexpr int kWords = (int)(sizeof(ft_stats) / 8);
-    if (threadIdx.x < kWords) {
-        __threadfence();
-        unsigned long long *w = reinterpret_cast<unsigned long long *>(&sr.slot->s) + threadIdx.x;
-        reinterpret_cast<unsigned long long *>(user)[threadIdx.x] = __ldcg(w);
-        *w = (threadIdx.x < FT_MAX_R || threadIdx.x == 2 * FT_MAX_R) ? 0ull : ~0ull;
-        if (sr.flag) __threadfence_system();   // the copy reaches the host before the flag
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sr.slot->done = 0;
-        // the slot's reset values are visible on the device before the free
-        // flag is written, so the vote the host launches on the slot once it
-        // reads the flag sees them; only the GPU reads the slot
-        __threadfence();
-        *reinterpret_cast<volatile unsigned int *>(sr.busy) = 0u;
-        if (sr.flag) *reinterpret_cast<volatile unsigned long long *>(sr.flag) = sr.seq;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K1: persistent single-task voter.  Warps take 4 KiB blocks in grid-stride
-// order; consecutive warps of a CTA take consecutive blocks.  PF: each warp
-// prefetches its next block into L2.  JB: 16-byte vectors per lane loaded per
-// sub-batch.
-//
-// The kernel is always launched as a programmatic dependent of the kernel
-// before it in the stream, and lets the kernel after it launch once its own
-// CTAs have voted their blocks.
-// Before it waits for its predecessor it asks L2 for the warp's first block
-// of every replica (L2 is the device's point of coherence, so early lines are
-// never stale) and copies the CRC tables into shared memory; it reads the
-// replicas only after the wait.  With a slot the predecessor is whatever the
-// caller ran before; without one it is the statistics reset, which touches
-// only the statistics, and the wait moves to just before they are added.
-// ---------------------------------------------------------------------------
-template <int K, int R, int W, bool PF, int JB, bool SMALL>
-__global__ void __launch_bounds__(W * 32, 1) vote_kernel(const TaskArgs a, const SlotRef sr)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *s_crc = reinterpret_cast<uint32_t *>(smem);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned long long step = (unsigned long long)gridDim.x * W;
-    const unsigned long long gw = (unsigned long long)blockIdx.x * W + w;
-    if (lane < R && gw < a.nfull) prefetch_l2(rep_for_lane<R>(a, lane) + gw * kBlockBytes, kBlockBytes);
-    load_crc_tables<W>(s_crc);
-    if (sr.wait_early) pdl_wait();  // the predecessor's writes (possibly our replicas) are visible
-    __syncthreads();
-    CrcLane L;
-    L.init(lane);
-    LaneStats<R> st;
-    st.init();
-    for (unsigned long long b = gw; b < a.nfull; b += step)
-        vote_full_block<K, R, JB, SMALL>(a, b, PF ? b + step : ~0ull, s_crc, L, st, lane);
-    if (a.tail_bytes && a.nfull % step == gw) {
-        // the partial last block goes to the warp whose turn it would be
-        LaneStats<R> ts;
-        ts.init();
-        vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
-        st.merge(ts);
-    }
-    // Only now may the next kernel's CTAs launch: one released at the start
-    // would take SMs (a voter CTA holds an SM's shared memory) and sit in its
-    // wait while this kernel votes, keeping other streams' work off them.
-    pdl_release();
-    if (sr.slot) {
-        st.flush(&sr.slot->s, lane);
-        slot_finish(sr, a.stats);
-    } else {
-        if (!sr.wait_early) pdl_wait();   // the statistics reset has completed
-        st.flush(a.stats, lane);
-    }
-}
-
 // Launches one shape.  With a slot the statistics reset is not needed; the
 // kernel is a programmatic dependent of the caller's previous kernel.
 template <int K, int R, int kVoteWarps, bool PF, int JB, bool SMALL = false>
 static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch *cfg, const SlotRef &sr)
 {
-    auto fn = vote_kernel<K, R, kVoteWarps, PF, JB, SMALL>;
+    const void *fn = reinterpret_cast<const void *>(vote_kernel<K, R, kVoteWarps, PF, JB, SMALL>);
+    if (sr.flag) {
+        // the server's vote, which also writes its completion flag
+        if constexpr (kDefaultShape<K, R, kVoteWarps, PF, JB, SMALL>)
+            fn = flagged_vote_kernel<K, R, kVoteWarps, PF, JB, SMALL>();
+        else
+            return FT_EINVAL;
+    }
     const size_t smem = kSmemBytes;
     int sms = 0, per_sm = 0;
-    int rc = occupancy(reinterpret_cast<const void *>(fn), kVoteWarps * 32, smem, &sms, &per_sm);
+    int rc = occupancy(fn, kVoteWarps * 32, smem, &sms, &per_sm);
     if (rc != FT_OK) return rc;
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < per_sm) per_sm = cfg->ctas_per_sm;
     const unsigned long long nblk = a.nfull + (a.tail_bytes ? 1 : 0);
@@ -370,7 +276,8 @@ static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&lc, fn, a, sr);
+    void *args[] = {const_cast<TaskArgs *>(&a), const_cast<SlotRef *>(&sr)};
+    const cudaError_t e = cudaLaunchKernelExC(&lc, fn, args);
     if (e != cudaSuccess) return cuda_fail(e);
     return check_launch(1);
 }
@@ -386,7 +293,6 @@ static int launch_vote_shape(const TaskArgs &a, cudaStream_t s, const VoteLaunch
 // the SMALL form of the block voter (two CRC chains per lane, R = 3 pairwise
 // masks kept in registers).
 constexpr unsigned long long kSmallVoteBlocks = 32768;
-constexpr int kTinyWarps = 8;
 // Up to 4096 blocks (16 MiB of output) the 16-warp shape also takes the SMALL
 // block form: f32 R = 3 3 x 2M 13.1 -> 10.7 us, 3 x 4M 18.6 -> 16.9 us;
 // from 16384 blocks on it no longer gains (3 x 16M 48.2 against 48.5 us, 5 x 8M
@@ -493,6 +399,7 @@ int preload_vote_kernels()
         (rc = preload_vote_k<K_B1>()) != FT_OK || (rc = preload_vote_k<K_B4>()) != FT_OK ||
         (rc = preload_vote_k<K_B8>()) != FT_OK)
         return rc;
+    if ((rc = preload_flagged_vote_kernels()) != FT_OK) return rc;
     int dev = 0;
     const cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
