@@ -296,7 +296,16 @@ typedef struct ft_server_config {
                                    request's (a much smaller one would wait for the large one it
                                    is packed with); on the last free slot everything waiting is
                                    packed: 0 = 8, -1 = no limit, else 2 or more */
-    int32_t  pad_;
+    int32_t  resident;          /* 0 = batches (above).  1 = resident mode (no batches, no
+                                   launch per request): one persistent kernel on every SM takes
+                                   each request from a host-mapped mailbox and votes it in
+                                   tiles, the request with the fewest tiles left first;
+                                   max_slots, streams, tile_blocks, max_batch_bytes,
+                                   reserved_sms and size_ratio are not used.  2 = shared: the
+                                   batches as with 0, and each request whose output has fewer
+                                   4 KiB blocks than the resident kernel has voting warps goes
+                                   to a resident kernel on the reserved_sms SMs that the batches
+                                   leave free (32 when reserved_sms is 0 or -1) */
 } ft_server_config;
 
 typedef struct ft_result {
@@ -327,6 +336,22 @@ typedef struct ft_result {
  * batch before it sleeps.  Creation loads every kernel the server can launch
  * (a few tens of milliseconds the first time in a process), so that no
  * request pays CUDA's lazy loading of a kernel at its first launch.
+ *
+ * With cfg->resident = 1 there are no batches: the thread hands each request
+ * to one of 32 device slots through a host-mapped mailbox, and one persistent
+ * voter kernel (one CTA per SM, launched when a request arrives and nothing
+ * is running) admits it and votes it in tiles, the request with the fewest
+ * tiles left first, so a small request is not held behind a large one.  Each
+ * request completes on its own (statistics and flag to host-mapped memory;
+ * to desc->stats too when given).  The kernel leaves once nothing has arrived
+ * for cfg->idle_spin_us (2 ms by default) and every request on it is done;
+ * while requests keep arriving it holds every SM, so other kernels of the
+ * process (and a second resident server on the same GPU) wait for it to
+ * leave.  Requests beyond the 32 slots wait on the host.  With
+ * cfg->resident = 2 the same kernel runs on the reserved SMs only and takes
+ * the small requests (fewer 4 KiB blocks of output than its 511 voting warps
+ * with the default 32 SMs), with no launch per request, while the larger ones
+ * are batched and launched as with 0.
  * Returns FT_OK, FT_EINVAL, FT_ENOMEM or FT_ECUDA. */
 int ft_server_create(ft_server **srv, const ft_server_config *cfg);
 

@@ -6,46 +6,9 @@
 #include "batched.h"
 #include "common.cuh"
 #include "runtime.h"
+#include "tile_vote.cuh"
 
 namespace ftv {
-
-// Votes tile k of task a (its blocks, and its partial last block when the
-// tile holds it) and adds the tile's statistics to the task's.  Kept out of
-// line, so that each (kind, R) instance has its own register allocation
-// inside the one kernel.
-template <int K, int R>
-__device__ __noinline__ void mixed_tile(const TaskArgs &a, unsigned long long k, int tile_blocks, const uint32_t *s_crc,
-                                        const CrcLane &L, int lane)
-{
-    LaneStats<R> st;
-    st.init();
-    const unsigned long long b0 = k * (unsigned long long)tile_blocks;
-    const unsigned long long b1 = min(b0 + (unsigned long long)tile_blocks, a.nfull);
-    for (unsigned long long b = b0; b < b1; ++b) vote_full_block<K, R>(a, b, ~0ull, s_crc, L, st, lane);
-    if (a.tail_bytes && a.nfull / tile_blocks == k) {
-        LaneStats<R> ts;
-        ts.init();
-        vote_tail_block<K, R>(a, a.nfull, s_crc, L, ts, lane);
-        st.merge(ts);
-    }
-    st.flush(a.stats, lane);
-}
-
-template <int K>
-__device__ __forceinline__ void mixed_tile_k(const TaskArgs &a, unsigned long long k, int tile_blocks,
-                                             const uint32_t *s_crc, const CrcLane &L, int lane)
-{
-    switch (a.R) {
-    case 2: mixed_tile<K, 2>(a, k, tile_blocks, s_crc, L, lane); break;
-    case 3: mixed_tile<K, 3>(a, k, tile_blocks, s_crc, L, lane); break;
-    case 4: mixed_tile<K, 4>(a, k, tile_blocks, s_crc, L, lane); break;
-    case 5: mixed_tile<K, 5>(a, k, tile_blocks, s_crc, L, lane); break;
-    case 6: mixed_tile<K, 6>(a, k, tile_blocks, s_crc, L, lane); break;
-    case 7: mixed_tile<K, 7>(a, k, tile_blocks, s_crc, L, lane); break;
-    case 8: mixed_tile<K, 8>(a, k, tile_blocks, s_crc, L, lane); break;
-    default: break;
-    }
-}
 
 template <int W>
 __global__ void __launch_bounds__(W * 32, 1) batched_mixed_kernel(const MixedDev g)
@@ -64,15 +27,7 @@ __global__ void __launch_bounds__(W * 32, 1) batched_mixed_kernel(const MixedDev
         if (tg >= g.total_tiles) break;
         const int t = (int)g.tile_task[tg];
         const TaskArgs a = g.tasks[t];
-        const unsigned long long k = tg - g.tile_first_global[t];
-        switch (a.kind) {
-        case K_F32: mixed_tile_k<K_F32>(a, k, g.tile_blocks, s_crc, L, lane); break;
-        case K_F64: mixed_tile_k<K_F64>(a, k, g.tile_blocks, s_crc, L, lane); break;
-        case K_B1: mixed_tile_k<K_B1>(a, k, g.tile_blocks, s_crc, L, lane); break;
-        case K_B4: mixed_tile_k<K_B4>(a, k, g.tile_blocks, s_crc, L, lane); break;
-        case K_B8: mixed_tile_k<K_B8>(a, k, g.tile_blocks, s_crc, L, lane); break;
-        default: break;
-        }
+        mixed_tile_any(a, tg - g.tile_first_global[t], g.tile_blocks, 0ull, nullptr, s_crc, L, lane);
     }
 }
 

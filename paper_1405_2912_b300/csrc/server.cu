@@ -28,6 +28,7 @@
 
 #include "batched.h"
 #include "ftvote.h"
+#include "resident.h"
 #include "runtime.h"
 
 namespace {
@@ -148,6 +149,35 @@ ft_stats initial_stats()
     return st;
 }
 
+// The resident mode (ft_server_config.resident): no batches and no launch per
+// request.  The worker hands each request to a free device slot through a
+// host-mapped mailbox and keeps the resident kernel (resident.cu) running
+// while any slot is busy; the kernel writes each request's statistics and
+// flag to host-mapped memory when its last tile is voted.
+struct Resident {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;          // recorded after each launch: the kernel has left
+    uint8_t *dev = nullptr;              // device block: slots, counters, statistics
+    uint8_t *host = nullptr;             // host-mapped block: mailboxes, flags, statistics copies
+    ftv::ResDev g{};                     // the kernel's view of both
+    ftv::ResMail *mail = nullptr;        // host views of the host-mapped block
+    unsigned long long *mail_gen = nullptr;
+    unsigned int *quit = nullptr;
+    unsigned int *error = nullptr;
+    ft_stats *stats_out = nullptr;
+    unsigned long long *flags = nullptr;
+    unsigned long long slot_gen[ftv::kResSlots] = {};     // generation on slot j, 0 = free
+    unsigned long long slot_ticket[ftv::kResSlots] = {};
+    double slot_sent[ftv::kResSlots] = {};
+    unsigned long long gen = 0;          // last generation handed out
+    int voting_warps = 1;
+    int max_ctas = 0;                    // grid cap (the shared mode: the SMs the batches leave free)
+    bool running = false;                // launched, not yet seen to have left
+    double last_query = 0.0;
+    int failed = FT_OK;                  // the kernel reported an error or a launch failed
+    unsigned long long launches = 0;
+};
+
 }  // namespace
 
 struct ft_server {
@@ -174,6 +204,9 @@ struct ft_server {
     // bumped (under the lock) whenever there is something new for the worker:
     // an admitted request, a pause change or stop
     std::atomic<unsigned long long> version{0};
+    bool resident = false;             // resident-kernel memory allocated (resident = 1 or 2)
+    bool hybrid = false;               // resident = 2: small requests to the resident kernel
+    Resident res;
 };
 
 namespace {
@@ -570,6 +603,10 @@ int launch_slot(ft_server *s, int si, std::vector<ftv::TaskArgs> &args, bool any
 // requests exceed 200 us, and practically none exceed 2 ms.
 constexpr double kSpinUs = 2000.0;
 
+// Bound of every wait inside the resident kernel on another warp's progress
+// (a tile of the largest shape takes well under a millisecond).
+constexpr unsigned long long kResMaxWaitNs = 200000000ull;
+
 // Requests of a batch stay within this factor of the batch's first request's
 // bytes while another slot is free, unless the configuration says otherwise.
 // At 20k requests/s with 3 streams, 93 % of the requests above the p99 latency
@@ -592,6 +629,10 @@ double idle_spin_us(const ft_server *s)
     return s->cfg.idle_spin_us == 0 ? kSpinUs : s->cfg.idle_spin_us < 0 ? 0.0 : (double)s->cfg.idle_spin_us;
 }
 
+int res_pump(ft_server *s, bool *any);
+bool res_flagged(const Resident &R);
+void res_stop(Resident &R);
+
 void worker_main(ft_server *s)
 {
     cudaSetDevice(s->device);
@@ -599,12 +640,18 @@ void worker_main(ft_server *s)
     double idle_since = now_us();
     for (;;) {
         // 1. completions: requests whose flags are set, and batches whose
-        //    events have completed
+        //    events have completed; in the shared mode also the resident
+        //    kernel's, which then takes the small waiting requests
         bool any_busy = false;
         for (size_t i = 0; i < s->slots.size(); ++i) {
             if (!s->slots[i].busy) continue;
             reap_slot(s, (int)i);
             any_busy |= s->slots[i].busy;
+        }
+        if (s->hybrid) {
+            bool moved = false;
+            if (res_pump(s, &moved) > 0) any_busy = true;
+            if (moved) idle_since = now_us();
         }
         if (s->stop && !any_busy) break;
         int free_slot = -1;
@@ -626,6 +673,7 @@ void worker_main(ft_server *s)
                     changed = s->version.load(std::memory_order_acquire) != ver;
                     for (size_t k = 0; k < s->slots.size() && !changed; ++k)
                         if (s->slots[k].busy) changed = slot_progress(s->slots[k]);
+                    if (!changed && s->hybrid) changed = res_flagged(s->res);
                     if (!changed && !any_busy) std::this_thread::yield();
                 }
                 lk.lock();
@@ -734,10 +782,374 @@ void worker_main(ft_server *s)
         }
         idle_since = now_us();
     }
+    if (s->resident) {
+        lk.unlock();
+        res_stop(s->res);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Resident mode
+// ---------------------------------------------------------------------------
+
+// Tile of a resident request: about one tile per voting warp (up to 64
+// blocks), so a small request is spread over as many warps as it has blocks
+// and a large one is claimed once per warp.
+void res_tiles(const ft_server *s, const ftv::TaskArgs &a, unsigned long long *ntiles, int *tile_blocks)
+{
+    const unsigned long long nblk = a.nfull + (a.tail_bytes ? 1ull : 0ull);
+    const unsigned long long v = (unsigned long long)std::max(1, s->res.voting_warps);
+    // about one tile per voting warp (each claim and count is a round trip
+    // to a shared counter), at most 64 blocks
+    const unsigned long long tb = std::min(64ull, std::max(1ull, (nblk + v - 1ull) / v));
+    *tile_blocks = (int)tb;
+    *ntiles = nblk ? (nblk + (unsigned long long)tb - 1ull) / (unsigned long long)tb : 1ull;
+}
+
+// Request of slot j is done with `status` (lock held).
+void res_complete(ft_server *s, int j, double t, int status)
+{
+    Resident &R = s->res;
+    auto it = s->reqs.find(R.slot_ticket[j]);
+    if (it != s->reqs.end()) {
+        Request &r = it->second;
+        r.result = status == FT_OK ? R.stats_out[j] : initial_stats();
+        r.status = status;
+        r.done = true;
+        r.done_us = t;
+    }
+    s->completed += 1;
+    s->batch_span_us += t - R.slot_sent[j];
+    s->busy_now -= 1;
+    R.slot_gen[j] = 0;
+    s->cv_done.notify_all();
+}
+
+// Completions seen in the flags (lock held); returns the slots still busy.
+int res_reap(ft_server *s, double t, bool *any)
+{
+    Resident &R = s->res;
+    int busy = 0;
+    for (int j = 0; j < ftv::kResSlots; ++j) {
+        if (!R.slot_gen[j]) continue;
+        if (__atomic_load_n(&R.flags[j], __ATOMIC_ACQUIRE) == R.slot_gen[j]) {
+            res_complete(s, j, t, FT_OK);
+            *any = true;
+        } else {
+            ++busy;
+        }
+    }
+    return busy;
+}
+
+// Hands request tk to free slot j (lock held).
+void res_send_request(ft_server *s, int j, unsigned long long tk, Request &r)
+{
+    Resident &R = s->res;
+    const double t0 = now_us();
+    ftv::ResMail &m = R.mail[j];
+    m.args = r.args;
+    m.args.stats = R.g.stats + j;
+    m.user = r.user_stats;
+    res_tiles(s, r.args, &m.ntiles, &m.tile_blocks);
+    // small: fewer blocks than voting warps
+    m.urgent = r.args.nfull + (r.args.tail_bytes ? 1ull : 0ull) < (unsigned long long)R.voting_warps;
+    m.gen = ++R.gen;
+    m.pad_ = 0;
+    R.slot_gen[j] = m.gen;
+    R.slot_ticket[j] = tk;
+    // the mailbox is written before its generation is published
+    __atomic_store_n(&R.mail_gen[j], m.gen, __ATOMIC_RELEASE);
+    const double t1 = now_us();
+    R.slot_sent[j] = t1;
+    r.launch_us = t0;
+    r.launched_us = t1;
+    s->queue_us += t0 - r.submit_us;
+    s->launch_host_us += t1 - t0;
+    s->batches += 1;
+    s->batched_requests += 1;
+    s->busy_now += 1;
+    s->busy_max = std::max(s->busy_max, s->busy_now);
+}
+
+// Hands the oldest waiting request to free slot j (lock held).
+bool res_send(ft_server *s, int j)
+{
+    while (!s->pending.empty()) {
+        const unsigned long long tk = s->pending.front();
+        s->pending.pop_front();
+        auto it = s->reqs.find(tk);
+        if (it == s->reqs.end()) continue;
+        res_send_request(s, j, tk, it->second);
+        return true;
+    }
+    return false;
+}
+
+// The kernel has left (or failed): with an error every request on the
+// device fails, and so do the waiting ones (lock held).
+void res_fail_all(ft_server *s, int status, double t)
+{
+    Resident &R = s->res;
+    for (int j = 0; j < ftv::kResSlots; ++j)
+        if (R.slot_gen[j]) res_complete(s, j, t, status);
+    while (!s->pending.empty()) {
+        auto it = s->reqs.find(s->pending.front());
+        s->pending.pop_front();
+        if (it == s->reqs.end()) continue;
+        it->second.result = initial_stats();
+        it->second.status = status;
+        it->second.done = true;
+        it->second.done_us = t;
+    }
+    s->cv_done.notify_all();
+}
+
+// Whether the resident kernel has left; notes a failure (lock held or not:
+// only the worker touches these fields).
+bool res_left(Resident &R)
+{
+    const cudaError_t q = cudaEventQuery(R.done);
+    if (q == cudaErrorNotReady) return false;
+    R.running = false;
+    if (q != cudaSuccess) R.failed = ftv::cuda_fail(q);
+    else if (__atomic_load_n(R.error, __ATOMIC_ACQUIRE) != 0u) R.failed = FT_ECUDA;
+    return true;
+}
+
+// The shared mode (ft_server_config.resident = 2), from the batch worker
+// (lock held): completions of the resident kernel, and every waiting request
+// with fewer blocks than the kernel's voting warps handed to it while it has
+// free slots; the kernel is launched when its slots are busy and it is not
+// running.  Returns its busy slots.  After a failure of the kernel its
+// requests fail and every later request takes the batches.
+int res_pump(ft_server *s, bool *any)
+{
+    Resident &R = s->res;
+    const double t = now_us();
+    int busy = res_reap(s, t, any);
+    if (R.running && t - R.last_query >= kEventCheckUs) {
+        R.last_query = t;
+        if (res_left(R)) busy = res_reap(s, t, any);
+    }
+    if (R.failed != FT_OK) {
+        for (int j = 0; j < ftv::kResSlots; ++j)
+            if (R.slot_gen[j]) res_complete(s, j, t, R.failed);
+        s->hybrid = false;
+        return 0;
+    }
+    if (!s->stop && !s->paused) {
+        int j = 0;
+        for (auto it = s->pending.begin(); it != s->pending.end() && busy < ftv::kResSlots;) {
+            auto rq = s->reqs.find(*it);
+            if (rq == s->reqs.end()) {
+                it = s->pending.erase(it);
+                continue;
+            }
+            const ftv::TaskArgs &a = rq->second.args;
+            if (a.nfull + (a.tail_bytes ? 1ull : 0ull) >= (unsigned long long)R.voting_warps) {
+                ++it;
+                continue;
+            }
+            while (R.slot_gen[j]) ++j;
+            res_send_request(s, j, *it, rq->second);
+            it = s->pending.erase(it);
+            ++busy;
+            *any = true;
+        }
+    }
+    if (busy && !R.running) {
+        R.g.epoch += 1;
+        int ctas = 0;
+        int rc = ftv::resident_launch(R.g, R.stream, R.max_ctas, &ctas);
+        cudaError_t e = cudaSuccess;
+        if (rc == FT_OK && (e = cudaEventRecord(R.done, R.stream)) != cudaSuccess) rc = ftv::cuda_fail(e);
+        if (rc != FT_OK) {
+            R.failed = rc;
+            return res_pump(s, any);
+        }
+        R.running = true;
+        R.launches += 1;
+        R.last_query = now_us();
+    }
+    return busy;
+}
+
+// Whether the resident kernel has completed a request (no lock: only the
+// worker changes the slots).
+bool res_flagged(const Resident &R)
+{
+    for (int j = 0; j < ftv::kResSlots; ++j)
+        if (R.slot_gen[j] && __atomic_load_n(&R.flags[j], __ATOMIC_ACQUIRE) == R.slot_gen[j]) return true;
+    return false;
+}
+
+// Tells the resident kernel to leave and waits for it (its waits are bounded).
+void res_stop(Resident &R)
+{
+    __atomic_store_n(R.quit, 1u, __ATOMIC_RELEASE);
+    if (R.running) cudaEventSynchronize(R.done);
+    R.running = false;
+}
+
+void res_worker(ft_server *s)
+{
+    cudaSetDevice(s->device);
+    Resident &R = s->res;
+    std::unique_lock<std::mutex> lk(s->mu);
+    double idle_since = now_us();
+    for (;;) {
+        double t = now_us();
+        bool any = false;
+        int busy = res_reap(s, t, &any);
+        // the kernel: has it left?  (queried at most every kEventCheckUs,
+        // and not while a request waits to be handed over)
+        if (R.running && t - R.last_query >= kEventCheckUs && (busy > 0 || s->pending.empty())) {
+            R.last_query = t;
+            if (res_left(R)) busy = res_reap(s, t, &any);   // its last flags
+        }
+        if (R.failed != FT_OK) {
+            res_fail_all(s, R.failed, t);
+            busy = 0;
+        }
+        if (s->stop && busy == 0) break;
+        // waiting requests to free slots
+        if (!s->stop && !s->paused && R.failed == FT_OK) {
+            for (int j = 0; j < ftv::kResSlots && !s->pending.empty(); ++j)
+                if (!R.slot_gen[j] && res_send(s, j)) {
+                    ++busy;
+                    any = true;
+                }
+        }
+        // the kernel runs while any slot is busy (it leaves by itself once
+        // idle; a request handed over as it left finds it gone here)
+        if (busy && !R.running && R.failed == FT_OK) {
+            R.g.epoch += 1;
+            int ctas = 0;
+            int rc = ftv::resident_launch(R.g, R.stream, R.max_ctas, &ctas);
+            cudaError_t e = cudaSuccess;
+            if (rc == FT_OK && (e = cudaEventRecord(R.done, R.stream)) != cudaSuccess) rc = ftv::cuda_fail(e);
+            if (rc != FT_OK) {
+                R.failed = rc;
+                continue;
+            }
+            R.running = true;
+            R.launches += 1;
+            R.last_query = now_us();
+        }
+        if (any || busy) idle_since = now_us();
+        // wait: poll while requests are on the device or shortly after the
+        // last activity, without holding the lock; else sleep
+        if (busy || now_us() - idle_since < idle_spin_us(s)) {
+            const unsigned long long ver = s->version.load(std::memory_order_acquire);
+            const double t_end = now_us() + kPollSliceUs;
+            lk.unlock();
+            for (bool changed = false; !changed && now_us() < t_end;) {
+                changed = s->version.load(std::memory_order_acquire) != ver;
+                for (int j = 0; j < ftv::kResSlots && !changed; ++j)
+                    changed = R.slot_gen[j] && __atomic_load_n(&R.flags[j], __ATOMIC_ACQUIRE) == R.slot_gen[j];
+                if (!changed && !busy) std::this_thread::yield();
+            }
+            lk.lock();
+        } else {
+            s->cv_work.wait(lk);
+            idle_since = now_us();
+        }
+    }
+    lk.unlock();
+    res_stop(R);
+}
+
+// Device and host-mapped memory of the resident mode, the kernel loaded.
+int res_init(ft_server *s)
+{
+    Resident &R = s->res;
+    using ftv::kResSlots;
+    cudaError_t e;
+    int rc = ftv::resident_preload(R.max_ctas, &R.voting_warps);
+    if (rc != FT_OK) return rc;
+    if ((e = cudaStreamCreateWithFlags(&R.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming)) != cudaSuccess)
+        return ftv::cuda_fail(e);
+    // device block: slots | next | meta | done | admitted | fin | beat, progress | active, urgent, stop | stats
+    const size_t o_slots = 0;
+    const size_t o_next = o_slots + sizeof(ftv::ResSlot) * kResSlots;
+    const size_t o_meta = o_next + 8 * kResSlots;
+    const size_t o_done = o_meta + 8 * kResSlots;
+    const size_t o_adm = o_done + 8 * kResSlots;
+    const size_t o_fin = o_adm + 8 * kResSlots;
+    const size_t o_beat = o_fin + 8 * kResSlots;
+    const size_t o_act = o_beat + 16;
+    const size_t o_stats = (o_act + 16 + 255) & ~size_t(255);
+    const size_t dev_bytes = o_stats + sizeof(ft_stats) * kResSlots;
+    // host-mapped block: mailboxes | mail_gen | flags | quit, error | stats copies
+    const size_t h_mail = 0;
+    const size_t h_gen = h_mail + sizeof(ftv::ResMail) * kResSlots;
+    const size_t h_flags = h_gen + 8 * kResSlots;
+    const size_t h_ctl = h_flags + 8 * kResSlots;
+    const size_t h_stats = (h_ctl + 8 + 255) & ~size_t(255);
+    const size_t host_bytes = h_stats + sizeof(ft_stats) * kResSlots;
+    if ((e = cudaMalloc(&R.dev, dev_bytes)) != cudaSuccess) return ftv::cuda_fail(e);
+    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&R.host), host_bytes, cudaHostAllocMapped)) != cudaSuccess)
+        return ftv::cuda_fail(e);
+    std::memset(R.host, 0, host_bytes);
+    uint8_t *hd = nullptr;
+    if ((e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&hd), R.host, 0)) != cudaSuccess)
+        return ftv::cuda_fail(e);
+    // the device block at its initial values: zero counters, initial statistics
+    std::vector<uint8_t> init(dev_bytes, 0);
+    const ft_stats st0 = initial_stats();
+    for (int j = 0; j < kResSlots; ++j) std::memcpy(init.data() + o_stats + sizeof(ft_stats) * j, &st0, sizeof(st0));
+    if ((e = cudaMemcpy(R.dev, init.data(), dev_bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return ftv::cuda_fail(e);
+    R.mail = reinterpret_cast<ftv::ResMail *>(R.host + h_mail);
+    R.mail_gen = reinterpret_cast<unsigned long long *>(R.host + h_gen);
+    R.flags = reinterpret_cast<unsigned long long *>(R.host + h_flags);
+    R.quit = reinterpret_cast<unsigned int *>(R.host + h_ctl);
+    R.error = R.quit + 1;
+    R.stats_out = reinterpret_cast<ft_stats *>(R.host + h_stats);
+    ftv::ResDev &g = R.g;
+    g.mail = reinterpret_cast<const ftv::ResMail *>(hd + h_mail);
+    g.mail_gen = reinterpret_cast<const unsigned long long *>(hd + h_gen);
+    g.flags = reinterpret_cast<unsigned long long *>(hd + h_flags);
+    g.quit = reinterpret_cast<const unsigned int *>(hd + h_ctl);
+    g.error = reinterpret_cast<unsigned int *>(hd + h_ctl) + 1;
+    g.stats_out = reinterpret_cast<ft_stats *>(hd + h_stats);
+    g.slots = reinterpret_cast<ftv::ResSlot *>(R.dev + o_slots);
+    g.next = reinterpret_cast<unsigned long long *>(R.dev + o_next);
+    g.meta = reinterpret_cast<unsigned long long *>(R.dev + o_meta);
+    g.done = reinterpret_cast<unsigned long long *>(R.dev + o_done);
+    g.admitted = reinterpret_cast<unsigned long long *>(R.dev + o_adm);
+    g.fin = reinterpret_cast<unsigned long long *>(R.dev + o_fin);
+    g.beat = reinterpret_cast<unsigned long long *>(R.dev + o_beat);
+    g.progress = g.beat + 1;
+    g.active = reinterpret_cast<unsigned int *>(R.dev + o_act);
+    g.urgent = g.active + 1;
+    g.stop = g.active + 2;
+    g.stats = reinterpret_cast<ft_stats *>(R.dev + o_stats);
+    const double idle_us = idle_spin_us(s) > 0.0 ? idle_spin_us(s) : kSpinUs;
+    g.idle_ns = (unsigned long long)(idle_us * 1e3);
+    g.max_wait_ns = kResMaxWaitNs;
+    g.epoch = 0;
+    return FT_OK;
+}
+
+void res_free(Resident &R)
+{
+    if (R.running && R.quit) {
+        __atomic_store_n(R.quit, 1u, __ATOMIC_RELEASE);
+        cudaEventSynchronize(R.done);
+    }
+    if (R.stream) cudaStreamSynchronize(R.stream);
+    if (R.done) cudaEventDestroy(R.done);
+    if (R.stream) cudaStreamDestroy(R.stream);
+    if (R.dev) cudaFree(R.dev);
+    if (R.host) cudaFreeHost(R.host);
 }
 
 void free_server(ft_server *s)
 {
+    if (s->resident) res_free(s->res);
     for (auto &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
@@ -771,7 +1183,8 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     *out = nullptr;
     if (cfg->mem_budget_bytes == 0 || cfg->max_slots < 1 || cfg->max_slots > 65536 || cfg->streams < 1 ||
         cfg->streams > 8 || cfg->tile_blocks < 0 || cfg->tile_blocks > 64 || cfg->max_inflight < 0 ||
-        cfg->reserved_sms < -1 || cfg->idle_spin_us < -1 || cfg->size_ratio < -1 || cfg->size_ratio == 1)
+        cfg->reserved_sms < -1 || cfg->idle_spin_us < -1 || cfg->size_ratio < -1 || cfg->size_ratio == 1 ||
+        cfg->resident < 0 || cfg->resident > 2)
         return FT_EINVAL;
     ft_server *s = new (std::nothrow) ft_server();
     if (!s) return FT_ENOMEM;
@@ -783,6 +1196,17 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     if (e != cudaSuccess) {
         delete s;
         return ftv::cuda_fail(e);
+    }
+    if (cfg->resident == 1) {
+        s->resident = true;
+        int rc = res_init(s);
+        if (rc != FT_OK) {
+            free_server(s);
+            return rc == FT_ECUDA && ftv::g_last_cuda == cudaErrorMemoryAllocation ? FT_ENOMEM : rc;
+        }
+        s->worker = std::thread(res_worker, s);
+        *out = s;
+        return FT_OK;
     }
     s->slots.resize(cfg->streams);
     int rc = FT_OK;
@@ -815,6 +1239,13 @@ int ft_server_create(ft_server **out, const ft_server_config *cfg)
     }
     // every kernel a request may launch is loaded now, not at the request's launch
     if (rc == FT_OK && (rc = ftv::preload_vote_kernels()) == FT_OK) rc = ftv::preload_group_kernels();
+    if (rc == FT_OK && cfg->resident == 2) {
+        // the resident kernel on the SMs the batches leave free
+        s->resident = s->hybrid = true;
+        const int reserve = cfg->reserved_sms > 0 ? cfg->reserved_sms : kReservedSms;
+        s->res.max_ctas = reserve;
+        rc = res_init(s);
+    }
     if (rc != FT_OK) {
         free_server(s);
         return rc == FT_ECUDA && ftv::g_last_cuda == cudaErrorMemoryAllocation ? FT_ENOMEM : rc;

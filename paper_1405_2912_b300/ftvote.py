@@ -76,7 +76,7 @@ class ft_server_config(ctypes.Structure):
                 ("reserved_sms", ctypes.c_int32),
                 ("idle_spin_us", ctypes.c_int32),
                 ("size_ratio", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("resident", ctypes.c_int32)]
 
 
 class ft_result(ctypes.Structure):

@@ -86,6 +86,10 @@ def test_server_config_validation(fv):
                 (1 << 30, 16, 2, 8, 0, 0, -2)]:
         cfg = fv.ft_server_config(*bad)
         assert fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)) == fv.FT_EINVAL
+    for resident in (-1, 3):
+        cfg = fv.ft_server_config(1 << 30, 16, 2, 8, 0)
+        cfg.resident = resident
+        assert fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)) == fv.FT_EINVAL
     assert fv.ft_server_create(None, None) == fv.FT_EINVAL
     assert fv.ft_submit(None, None, None) == fv.FT_EINVAL
     assert fv.ft_poll(None, 1, 0, None) == fv.FT_EINVAL
