@@ -483,6 +483,10 @@ def batched_summary(b):
     return out
 
 
+def _r(x):
+    return None if x is None else round(x)
+
+
 def serving_summary(sv):
     """p50 / p99 latency and throughput of each serving arm at each rate."""
     if not sv:
@@ -493,14 +497,18 @@ def serving_summary(sv):
         if not r:
             continue
         arms = {}
-        for arm in ("continuous_batching", "unbatched", "plain_ft_vote"):
+        for arm in ("continuous_batching", "batch_launch", "unbatched", "plain_ft_vote"):
             a = r.get(arm)
             if not a:
                 continue
-            arms[arm] = {"p50_us": a["p50_us"], "p99_us": a["p99_us"], "req_per_s": a["req_per_s"],
-                         "p99_us_replays": a.get("p99_us_replays")}
-            if "mean_requests_per_batch" in a:
-                arms[arm]["req_per_batch"] = a["mean_requests_per_batch"]
+            # to the microsecond and the request per second; every replay's
+            # p99 beside the median for continuous batching and plain ft_vote
+            # (the other arms' in serving_detail)
+            reps = a.get("p99_us_replays")
+            arms[arm] = {"p50_us": _r(a["p50_us"]), "p99_us": _r(a["p99_us"]), "req_per_s": _r(a["req_per_s"])}
+            if arm in ("continuous_batching", "plain_ft_vote"):
+                arms[arm]["p99_us_replays"] = [round(x) for x in reps] if reps else reps
+            if arm == "continuous_batching" and "launch_host_us_per_batch" in a:
                 arms[arm]["launch_host_us_per_batch"] = a["launch_host_us_per_batch"]
         out[rate_key] = arms
     return out
@@ -624,10 +632,13 @@ SERVE_STREAMS = 4
 def run_serving(args, dev):
     """Poisson arrivals of votes with n log-uniform 4K..16M, R in {3, 5},
     f32/f64, under a 40 GB budget, replicas resident: continuous batching
-    (batches capped at 1 GB of request bytes) against one-request batches on
-    the same 4 streams, and against plain ft_vote calls issued at each arrival
-    on 4 streams in turn (no server), at the workload's 20k requests/s and at
-    three times that load."""
+    (the server's shared mode: requests with fewer 4 KiB output blocks than
+    the resident voter's warps to the resident voter on the 32 SMs that the
+    batches leave free, the others in batches capped at 1 GB of request
+    bytes) against the same server with every request batched and launched,
+    against one-request batches on the same 4 streams, and against plain
+    ft_vote calls issued at each arrival on 4 streams in turn (no server), at
+    the workload's 20k requests/s and at three times that load."""
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     from paper_1405_2912_b300 import serving
@@ -665,14 +676,19 @@ def run_serving(args, dev):
         # p99 are listed beside it): one replay's tail moves with the host's
         # scheduling
         warm = min(len(reqs), 300)
-        runs = {"plain_ft_vote": [], "continuous_batching": [], "unbatched": []}
+        runs = {"plain_ft_vote": [], "continuous_batching": [], "batch_launch": [], "unbatched": []}
         for _ in range(max(1, args.serve_reps)):
             # the plain arm: one ft_vote per request on the streams in turn, no server
             serving.replay_plain(plain_descs, arrivals[:warm] - arrivals[0], payload[:warm], nstreams=SERVE_STREAMS)
             r = serving.replay_plain(plain_descs, arrivals, payload, nstreams=SERVE_STREAMS)
             runs["plain_ft_vote"].append(serving.summarize(r, per_req))
-            for name, slots, cap in (("continuous_batching", 4096, 1 << 30), ("unbatched", 1, 0)):
+            # continuous batching: small requests to the resident voter on the
+            # SMs the batches leave free, the others batched and launched;
+            # batch_launch: every request batched and launched
+            for name, slots, cap, resident in (("continuous_batching", 4096, 1 << 30, 2),
+                                               ("batch_launch", 4096, 1 << 30, 0), ("unbatched", 1, 0, 0)):
                 cfg = fv.ft_server_config(int(40e9), slots, SERVE_STREAMS, 0, 0, cap)
+                cfg.resident = resident
                 srv = ctypes.c_void_p()
                 fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
                 try:
@@ -951,7 +967,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the request stream (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-pool", type=int, default=64)
-    ap.add_argument("--serve-reps", type=int, default=5, help="replays of each serving arm (the median p99 is reported)")
+    ap.add_argument("--serve-reps", type=int, default=7, help="replays of each serving arm (the median p99 is reported)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.warmup < 3 and args.impl == "ours":
