@@ -20,7 +20,7 @@
 // Every wait is bounded.  The admitting warp leaves once nothing has arrived
 // for idle_ns and every admitted request is done (the host relaunches the
 // kernel for the next request), when the host sets *quit, or, with an error
-// code, when requests are on the device but no tile has been voted for
+// code, when requests are on the device but none has completed for
 // max_wait_ns.  A voting warp waits for work only while the admitting warp
 // keeps beating (its loop counter); it leaves when that warp has left, or,
 // with an error code, when the beat stops for max_wait_ns.
