@@ -67,7 +67,8 @@ def test_batched_full_size():
         assert torch.equal(o, t.out[:t.nbytes]) and torch.equal(c, t.crc[:t.nb]) and torch.equal(s, t.stats), i
 
 
-def test_serving_full_stream():
+@pytest.mark.parametrize("resident", [0, 2])    # 2: small requests on the resident voter kernel
+def test_serving_full_stream(resident):
     import torch
     from paper_1405_2912_b300 import ftvote as fv
     from paper_1405_2912_b300 import serving
@@ -85,6 +86,7 @@ def test_serving_full_stream():
         d.stats = None
         descs.append(d)
     cfg = fv.ft_server_config(int(40e9), 4096, 3, 0, 0)
+    cfg.resident = resident
     srv = ctypes.c_void_p()
     fv.check(fv.ft_server_create(ctypes.byref(srv), ctypes.byref(cfg)), "ft_server_create")
     seen = []
