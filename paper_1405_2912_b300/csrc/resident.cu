@@ -254,12 +254,13 @@ __device__ __forceinline__ void read_slot(const ResDev &g, int j, ResSlot &sl)
 }
 
 // The (kind, R) tile routine of the slot's request, out of line so that the
-// scheduling loop around it stays small.
+// scheduling loop around it stays small; the latency form of the block voter
+// (most of this kernel's tiles are single blocks of small requests).
 __device__ __noinline__ unsigned long long vote_slot_tile(const ResSlot &sl, unsigned long long k,
                                                           unsigned long long b_begin, const unsigned int *preempt,
                                                           const uint32_t *s_crc, const CrcLane &L, int lane)
 {
-    return mixed_tile_any(sl.args, k, sl.tile_blocks, b_begin, preempt, s_crc, L, lane);
+    return mixed_tile_any<true>(sl.args, k, sl.tile_blocks, b_begin, preempt, s_crc, L, lane);
 }
 
 // Counts a voted tile of slot j (after its statistics); the warp that

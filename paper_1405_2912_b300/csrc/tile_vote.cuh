@@ -21,7 +21,9 @@ static __device__ const unsigned int g_never_preempt = 0u;
 // added); otherwise it returns kTileDone.  Kept out of line, so that each
 // (kind, R) instance has its own register allocation inside the one kernel.
 // A task of no elements has one tile of no blocks, which adds nothing.
-template <int K, int R>
+// SMALL: the latency form of the block voter (see vote_full_block), for a
+// kernel whose tiles are mostly single blocks of small tasks.
+template <int K, int R, bool SMALL>
 __device__ __noinline__ unsigned long long mixed_tile(const TaskArgs &a, unsigned long long k, int tile_blocks,
                                                       unsigned long long b_begin, const unsigned int *preempt,
                                                       const uint32_t *s_crc, const CrcLane &L, int lane)
@@ -40,7 +42,7 @@ __device__ __noinline__ unsigned long long mixed_tile(const TaskArgs &a, unsigne
         // load is in flight while the block is voted
         unsigned int u = 0;
         if (lane == 0 && (b + 1 < b1 || tail)) u = *pw;
-        vote_full_block<K, R>(a, b, ~0ull, s_crc, L, st, lane);
+        vote_full_block<K, R, kSubBatch<K, R>, SMALL>(a, b, ~0ull, s_crc, L, st, lane);
         if (__shfl_sync(0xFFFFFFFFu, u, 0)) {
             stop_at = b + 1;
             break;
@@ -56,34 +58,35 @@ __device__ __noinline__ unsigned long long mixed_tile(const TaskArgs &a, unsigne
     return stop_at;
 }
 
-template <int K>
+template <int K, bool SMALL>
 __device__ __forceinline__ unsigned long long mixed_tile_k(const TaskArgs &a, unsigned long long k, int tile_blocks,
                                                            unsigned long long b_begin, const unsigned int *preempt,
                                                            const uint32_t *s_crc, const CrcLane &L, int lane)
 {
     switch (a.R) {
-    case 2: return mixed_tile<K, 2>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case 3: return mixed_tile<K, 3>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case 4: return mixed_tile<K, 4>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case 5: return mixed_tile<K, 5>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case 6: return mixed_tile<K, 6>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case 7: return mixed_tile<K, 7>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case 8: return mixed_tile<K, 8>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 2: return mixed_tile<K, 2, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 3: return mixed_tile<K, 3, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 4: return mixed_tile<K, 4, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 5: return mixed_tile<K, 5, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 6: return mixed_tile<K, 6, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 7: return mixed_tile<K, 7, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case 8: return mixed_tile<K, 8, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
     default: return kTileDone;
     }
 }
 
 // The (kind, R) instance of the tile routine for task a.
+template <bool SMALL = false>
 __device__ __forceinline__ unsigned long long mixed_tile_any(const TaskArgs &a, unsigned long long k, int tile_blocks,
                                                              unsigned long long b_begin, const unsigned int *preempt,
                                                              const uint32_t *s_crc, const CrcLane &L, int lane)
 {
     switch (a.kind) {
-    case K_F32: return mixed_tile_k<K_F32>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case K_F64: return mixed_tile_k<K_F64>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case K_B1: return mixed_tile_k<K_B1>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case K_B4: return mixed_tile_k<K_B4>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
-    case K_B8: return mixed_tile_k<K_B8>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case K_F32: return mixed_tile_k<K_F32, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case K_F64: return mixed_tile_k<K_F64, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case K_B1: return mixed_tile_k<K_B1, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case K_B4: return mixed_tile_k<K_B4, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
+    case K_B8: return mixed_tile_k<K_B8, SMALL>(a, k, tile_blocks, b_begin, preempt, s_crc, L, lane);
     default: return kTileDone;
     }
 }
