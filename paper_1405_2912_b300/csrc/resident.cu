@@ -149,7 +149,6 @@ __device__ __noinline__ void admit_loop(const ResDev &g, int lane)
             atomicOr(g.active, fresh_mask);
             if (urgent_mask) atomicOr(g.urgent, urgent_mask);
         }
-        __threadfence();
         const bool busy = ld_relaxed_gpu(g.admitted + lane) != ld_relaxed_gpu(g.fin + lane);
         const unsigned busy_mask = __ballot_sync(full, busy);
         const unsigned long long t = gtime();
@@ -208,7 +207,7 @@ __device__ __noinline__ void hand_off(const ResDev &g, int j, const ResSlot &sl,
 // request's tile count; 0 when the claim lost a race (look again); -1 when
 // nothing in the mask is claimable.
 __device__ __noinline__ int claim_tile(const ResDev &g, unsigned mask, int lane, int *j_out,
-                                          unsigned long long *k_out, unsigned long long *nt_out)
+                                          unsigned long long *k_out, unsigned long long *nt_out, ResSlot *sl_out)
 {
     const unsigned full = 0xFFFFFFFFu;
     unsigned key = 0xFFFFFFFFu;
@@ -228,12 +227,20 @@ __device__ __noinline__ int claim_tile(const ResDev &g, unsigned mask, int lane,
     if (best == 0xFFFFFFFFu) return -1;
     const int j = (int)(best & 31u);
     const unsigned long long mj = __shfl_sync(full, mt, j);
+    // the slot, one word per lane, read while the claim is in flight: it is
+    // the request of the generation scanned (written before its claim
+    // counter), and the claim below keeps it only if that generation holds
+    unsigned long long w = 0;
+    if (lane < kSlotWords) w = __ldcg(reinterpret_cast<const unsigned long long *>(g.slots + j) + lane);
     unsigned long long v = 0;
     if (lane == 0) v = atomicAdd(g.next + j, 1ull);
     v = __shfl_sync(full, v, 0);
     const unsigned long long nt = mj & kResTileMask, k = v & kResTileMask;
     // another request took the slot since the scan, or its tiles are all taken
     if ((v >> kResGenShift) != (mj >> kResGenShift) || k >= nt) return 0;
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(sl_out);
+#pragma unroll
+    for (int i = 0; i < kSlotWords; ++i) d[i] = __shfl_sync(full, w, i);
     if (k + 1ull == nt && lane == 0) {
         atomicAnd(g.active, ~(1u << j));
         atomicAnd(g.urgent, ~(1u << j));
@@ -289,10 +296,11 @@ __device__ __noinline__ void vote_loop(const ResDev &g, const uint32_t *s_crc, i
         int j = 0;
         unsigned long long k = 0, nt = 0, b_begin = 0;
         bool resume = false;
+        ResSlot sl;
         if (held) {
             // urgent tiles first, then the tile put aside
             const unsigned urg = ld_acquire_gpu32(g.urgent);
-            const int c = urg ? claim_tile(g, urg, lane, &j, &k, &nt) : -1;
+            const int c = urg ? claim_tile(g, urg, lane, &j, &k, &nt, &sl) : -1;
             if (c == 0) continue;
             if (c < 0) {
                 j = hj;
@@ -300,9 +308,10 @@ __device__ __noinline__ void vote_loop(const ResDev &g, const uint32_t *s_crc, i
                 nt = hnt;
                 b_begin = hb;
                 resume = true;
+                read_slot(g, j, sl);
             }
         } else {
-            const int c = claim_tile(g, ld_acquire_gpu32(g.active), lane, &j, &k, &nt);
+            const int c = claim_tile(g, ld_acquire_gpu32(g.active), lane, &j, &k, &nt, &sl);
             if (c == 0) continue;
             if (c < 0) {
                 // nothing to claim: leave when the admitting warp has left,
@@ -322,8 +331,6 @@ __device__ __noinline__ void vote_loop(const ResDev &g, const uint32_t *s_crc, i
             }
             sleep_ns = 64;
         }
-        ResSlot sl;
-        read_slot(g, j, sl);
         // the tile put aside, and a fresh tile of a large request, stop
         // between blocks while an urgent request waits; an urgent tile, and
         // any tile voted while another is put aside, runs through
