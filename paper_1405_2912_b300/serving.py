@@ -136,6 +136,11 @@ def _replay_plain(descs, arrivals_s, payload_of, nstreams, start_delay_us):
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
     handles = [int(s.cuda_stream) for s in streams]
     events = [torch.cuda.Event() for _ in range(max(n, 1))]
+    # a torch event creates its CUDA event at its first record: record each
+    # once before the clock starts, so that the loop creates none
+    for k, e in enumerate(events):
+        e.record(streams[k % nstreams])
+    torch.cuda.synchronize()
     refs = [[ctypes.byref(d) for d in per_stream] for per_stream in descs]
     vote, clock = fv.ft_vote, fv.ft_clock_us
     queues = [collections.deque() for _ in range(nstreams)]
