@@ -203,9 +203,9 @@ __device__ __noinline__ void hand_off(const ResDev &g, int j, const ResSlot &sl,
 }
 
 // Scans the slots in `mask` (lane j: slot j) and claims the next tile of the
-// one with the fewest unclaimed tiles.  Returns 1 with the slot, tile and the
-// request's tile count; 0 when the claim lost a race (look again); -1 when
-// nothing in the mask is claimable.
+// one with the fewest unclaimed tiles.  Returns 1 with the slot, tile, the
+// request's tile count and the slot's contents (*sl_out); 0 when the claim
+// lost a race (look again); -1 when nothing in the mask is claimable.
 __device__ __noinline__ int claim_tile(const ResDev &g, unsigned mask, int lane, int *j_out,
                                           unsigned long long *k_out, unsigned long long *nt_out, ResSlot *sl_out)
 {
