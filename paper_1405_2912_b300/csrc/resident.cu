@@ -94,6 +94,21 @@ __device__ __forceinline__ void st_relaxed_sys32(unsigned int *p, unsigned int v
     asm volatile("st.relaxed.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_release_gpu(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Atomic add with acquire and release semantics at device scope: the
+// thread's earlier writes are visible to whoever sees the new value, and it
+// sees the writes of those whose adds came before.
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long *p, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 constexpr int kSlotWords = (int)(sizeof(ResSlot) / 8);
 constexpr int kStatWords = (int)(sizeof(ft_stats) / 8);   // mismatch[8], first[8], no_majority, first
 static_assert(kStatWords == 2 * FT_MAX_R + 2, "ft_stats layout");
@@ -133,8 +148,9 @@ __device__ __noinline__ void admit_loop(const ResDev &g, int lane)
             if (lane == 0) {
                 const unsigned long long g24 = (gj & 0xFFFFFFull) << kResGenShift;
                 st_relaxed_gpu(g.meta + jj, g24 | ntiles);
-                __threadfence();
-                atomicExch(g.next + jj, g24);   // claimable from here
+                // claimable from here: the release orders the slot and its
+                // tile count before the claim counter
+                st_release_gpu(g.next + jj, g24);
                 st_relaxed_gpu(g.admitted + jj, gj);
             }
         }
@@ -179,8 +195,10 @@ __device__ __noinline__ void admit_loop(const ResDev &g, int lane)
 // caller), the slot back to its initial values, then the flag.
 __device__ __noinline__ void hand_off(const ResDev &g, int j, const ResSlot &sl, int lane)
 {
-    // every warp that voted a tile of the request flushed its statistics and
-    // fenced before counting the tile, so they are final in L2
+    // every warp that voted a tile of the request counted it after its
+    // statistics with a release, and lane 0 of this warp counted the last
+    // with an acquire: the statistics are final in L2 (the other lanes read
+    // them after the shuffle that follows lane 0's count)
     __threadfence();
     if (lane < kStatWords) {
         unsigned long long *w = reinterpret_cast<unsigned long long *>(g.stats + j) + lane;
@@ -274,11 +292,11 @@ __device__ __noinline__ unsigned long long vote_slot_tile(const ResSlot &sl, uns
 // completes the request hands it off.
 __device__ __forceinline__ void finish_tile(const ResDev &g, int j, unsigned long long nt, const ResSlot &sl, int lane)
 {
+    // lane 0 made the tile's statistics atomics; its acquire-release count
+    // orders them before the count, and makes the last counter see every
+    // earlier tile's
     int last = 0;
-    if (lane == 0) {
-        __threadfence();
-        last = atomicAdd(g.done + j, 1ull) + 1ull == nt;
-    }
+    if (lane == 0) last = atom_add_acq_rel_gpu(g.done + j, 1ull) + 1ull == nt;
     if (__shfl_sync(0xFFFFFFFFu, last, 0)) hand_off(g, j, sl, lane);
 }
 
